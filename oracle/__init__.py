@@ -80,6 +80,8 @@ def _load():
         lib.or_substep.restype = ctypes.c_double
         lib.or_long_char.argtypes = [P, ctypes.c_int, dp, dp]
         lib.or_long_char.restype = None
+        lib.or_compute_dt.argtypes = [P, ctypes.POINTER(_Scheme), dp]
+        lib.or_compute_dt.restype = ctypes.c_double
         lib.or_snap.argtypes = [ctypes.c_double, ctypes.c_int]
         lib.or_snap.restype = ctypes.c_int
         _lib = lib
@@ -193,6 +195,12 @@ class Problem:
         dt = _load().or_substep(ctypes.byref(self.st), ctypes.byref(sc), _ptr(x), _ptr(tt), float(t_end),
                                 _ptr(bud), _ptr(N1))
         return float(tt[0]), dt, bud, N1
+
+    def compute_dt(self, x: np.ndarray, scheme: int = 3, K1=0.0, K3=0.0, K4=0.0) -> float:
+        """Eq. 4 minimum over all cells for the state x (trace included)."""
+        x = np.ascontiguousarray(x, np.float64).reshape(self.nz, self.ny, self.nx)
+        sc = _Scheme(int(scheme), float(K1), float(K3), float(K4), 0.0)
+        return _load().or_compute_dt(ctypes.byref(self.st), ctypes.byref(sc), _ptr(x))
 
     def run(self, x: np.ndarray, t: float, t_end: float, scheme: int = 3, max_steps: int = 10 ** 9,
             callback=None, **crit):

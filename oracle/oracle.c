@@ -95,10 +95,12 @@ static double bb_phi(double xnu, double theta) { return xnu * xnu / expm1(theta 
 typedef struct { double theta, sigma0, N; int moment; double mu; } bb_args;
 
 /* Integrand of the m-th moment: phi * sigma^m * exp(-sigma N), with the
- * "centred" second moment phi (sigma - mu)^2 exp(-sigma N) for m = 3. */
+ * "centred" second moment phi (sigma - mu)^2 exp(-sigma N) for m = 3 and the
+ * deficit phi * (exp(-sigma N) - 1) for m = 4. */
 static double bb_integrand(double xnu, const bb_args *a)
 {
     double s = a->sigma0 / (xnu * xnu * xnu);
+    if (a->moment == 4) return bb_phi(xnu, a->theta) * expm1(-s * a->N);
     double w = bb_phi(xnu, a->theta) * exp(-s * a->N);
     switch (a->moment) {
     case 0: return w;
@@ -199,7 +201,15 @@ int or_table_build(int kind, double Tbb, double sigma0, double numax_over_nu0,
         double mu = m1 / m0;
         a.moment = 3; a.mu = mu;
         double v = bb_moment(&a, 1.0, numax_over_nu0, m0 * mu * mu) / m0;
-        L[k] = log(m0 / Z);
+        if (m0 > 0.5 * Z) {
+            /* thin columns: ln(P/Q) = log1p(int phi (e^{-sigma N} - 1) / Z), no cancellation */
+            a.moment = 4;
+            double def = bb_moment(&a, 1.0, numax_over_nu0, Z - m0);
+            def = bb_moment(&a, 1.0, numax_over_nu0, fabs(def) > 0 ? fabs(def) : 1e-300);
+            L[k] = log1p(def / Z);
+        } else {
+            L[k] = log(m0 / Z);
+        }
         D1[k] = -N * mu;
         D2[k] = -N * mu + N * N * v;
     }
@@ -287,29 +297,37 @@ double or_tab_dlnp(const or_tab *T, double Na, double dN)
     static const double gx[3] = {-0.774596669241483377035853079956480, 0.0,
                                  0.774596669241483377035853079956480};
     static const double gw[3] = {5.0 / 9.0, 8.0 / 9.0, 5.0 / 9.0};
-    while (rem > 0.0) {
-        double lam = log(lo);
-        int k = (int)floor((lam - T->lnN_lo) / dl);
-        if (k > T->K - 2) k = T->K - 2;
-        if (k < 0) k = 0;
-        double Nk1 = exp(T->lnN_lo + (k + 1) * dl);
-        if (Nk1 <= lo && k < T->K - 2) { k++; Nk1 = exp(T->lnN_lo + (k + 1) * dl); }
-        double piece = (Nk1 - lo) < rem ? (Nk1 - lo) : rem;
-        if (!(piece > 0.0)) piece = rem;      /* a node rounded onto lo: finish here */
-        double len = log1p(piece / lo);       /* length of the piece in ln N */
-        double lam0 = T->lnN_lo + k * dl;
-        double y[6];
-        tab_node(T, k, y);
-        double sum = 0.0;
-        for (int g = 0; g < 3; g++) {
-            double lg = lam + 0.5 * len * (1.0 + gx[g]);
-            sum += gw[g] * herm5_deriv(y, (lg - lam0) / dl, dl);
-        }
-        acc += 0.5 * len * sum;
-        if (piece >= rem) break;
-        lo += piece;
-        rem -= piece;
+    /* integral of the interpolant's derivative over [lo, lo + piece] inside interval k */
+#define OR_PIECE(k_, lo_, piece_)                                                      \
+    do {                                                                               \
+        double len_ = log1p((piece_) / (lo_));                                         \
+        double lam_ = log(lo_), lam0_ = T->lnN_lo + (k_) * dl, y_[6], sum_ = 0.0;      \
+        tab_node(T, (k_), y_);                                                         \
+        for (int g = 0; g < 3; g++)                                                    \
+            sum_ += gw[g] * herm5_deriv(y_, (lam_ + 0.5 * len_ * (1.0 + gx[g]) - lam0_) / dl, dl); \
+        acc += 0.5 * len_ * sum_;                                                      \
+    } while (0)
+    int k = (int)floor((log(lo) - T->lnN_lo) / dl);
+    if (k > T->K - 2) k = T->K - 2;
+    if (k < 0) k = 0;
+    double Nk1 = exp(T->lnN_lo + (k + 1) * dl);
+    if (Nk1 <= lo && k < T->K - 2) { k++; Nk1 = exp(T->lnN_lo + (k + 1) * dl); }
+    if (rem <= Nk1 - lo) {                  /* the step stays inside one interval */
+        OR_PIECE(k, lo, rem);
+        return acc;
     }
+    OR_PIECE(k, lo, Nk1 - lo);              /* first partial interval */
+    rem -= Nk1 - lo;
+    double Nend = Nk1 + rem;
+    int k2 = (int)floor((log(Nend) - T->lnN_lo) / dl);
+    if (k2 > T->K - 2) k2 = T->K - 2;
+    if (k2 < k + 1) k2 = k + 1;
+    double Nk2 = exp(T->lnN_lo + k2 * dl);
+    if (Nk2 > Nend && k2 > k + 1) { k2--; Nk2 = exp(T->lnN_lo + k2 * dl); }
+    acc += T->L[k2] - T->L[k + 1];          /* whole intervals: node differences */
+    double last = (k2 == k + 1) ? rem : Nend - Nk2;
+    if (last > 0.0) OR_PIECE(k2, Nk2, last); /* last partial interval */
+#undef OR_PIECE
     return acc;
 }
 
@@ -1000,4 +1018,20 @@ int or_snap(double pos, int n)
     if (v < 0) v = 0;
     if (v > n) v = n;
     return (int)v;
+}
+
+/* The timestep interface (Sect. 2.1): trace x for every source and return the
+ * Eq. 4 minimum over all cells (+inf when no criterion limits it). */
+double or_compute_dt(const or_problem *p, const or_scheme *sc, const double *x)
+{
+    long ncell = (long)p->nx * p->ny * p->nz;
+    int S = p->nsrc;
+    double *N1 = (double *)malloc(sizeof(double) * ncell * (S > 0 ? S : 1));
+    double *xdot = (double *)malloc(sizeof(double) * ncell);
+    for (int s = 0; s < S; s++) or_trace(p, s, x, N1 + (long)s * ncell, NULL);
+    or_rates(p, x, N1, NULL, xdot);
+    double dt = crit_dt(p, sc, x, xdot);
+    free(N1);
+    free(xdot);
+    return dt;
 }

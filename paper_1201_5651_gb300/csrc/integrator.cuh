@@ -1,0 +1,537 @@
+// Per-cell integrator of the neutral-fraction ODE (Mackey 2012, Eq. 2 with the
+// temperature fixed and collisional ionisation off):
+//
+//     dx/dt = f(x) = -F(x) + c (1 - x)^2,   c = alpha_B n,
+//
+// where F(x) = sum_s F_s(x) is the photon-conserving photoionisation rate per
+// H atom with the entry columns frozen and the cell's own optical depth
+// evolving with x.  f is convex and strictly decreasing on [0,1], so x moves
+// monotonically to the unique root x_eq.
+//
+// Method (time-to-state inversion): with u = ln((x - x_eq)/(x0 - x_eq)),
+// du/dt = -D(u) where D = -(f(x_eq + d) - f(x_eq))/d > 0 (d = x - x_eq) is the
+// secant slope, evaluated from difference forms without cancellation.  The
+// elapsed time T(u) = int_u^0 du'/D(u') is accumulated over Gauss-Legendre
+// panels in u; the panel in which T reaches h is inverted through the
+// Legendre interpolant of 1/D on its nodes (no further evaluations).  Close
+// to equilibrium (|d| small against the scales on which F and the
+// recombination term bend) T(u) = T_t + (u_t - u)/D_inf + R(e^u) with R smooth
+// in w = e^u, integrated by one more Gauss rule in w.  The time integrals of
+// the recombination term (for the photon budget) and of exp(-b0 x) (for the
+// time-averaged attenuation of A1, Eq. 3) are accumulated on the same nodes.
+#pragma once
+#include "common.cuh"
+
+namespace oots {
+
+// Gauss-Legendre rules on [-1, 1] and Legendre polynomials at their nodes.
+template <int G> struct GL;
+template <> struct GL<4> {
+    static OOTS_HD __forceinline__ double x(int i) {
+        const double v[4] = {-0.8611363115940526, -0.3399810435848563, 0.3399810435848563, 0.8611363115940526};
+        return v[i];
+    }
+    static OOTS_HD __forceinline__ double w(int i) {
+        const double v[4] = {0.3478548451374538, 0.6521451548625461, 0.6521451548625461, 0.3478548451374538};
+        return v[i];
+    }
+};
+template <> struct GL<8> {
+    static OOTS_HD __forceinline__ double x(int i) {
+        const double v[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290, -0.1834346424956498,
+                             0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
+        return v[i];
+    }
+    static OOTS_HD __forceinline__ double w(int i) {
+        const double v[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873, 0.3626837833783620,
+                             0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
+        return v[i];
+    }
+};
+
+// Legendre polynomials P_0..P_{n-1} at s by the three-term recurrence.
+template <typename Real, int N>
+OOTS_HD __forceinline__ void legendre(Real s, Real *P)
+{
+    P[0] = Real(1);
+    if (N > 1) P[1] = s;
+#pragma unroll
+    for (int n = 1; n + 1 < N; n++) P[n + 1] = (Real(2 * n + 1) * s * P[n] - Real(n) * P[n - 1]) / Real(n + 1);
+}
+
+// Legendre coefficients of the degree G-1 interpolant through G Gauss nodal values.
+template <typename Real, int G>
+OOTS_HD __forceinline__ void leg_coeffs(const Real *v, Real *c)
+{
+#pragma unroll
+    for (int n = 0; n < G; n++) c[n] = Real(0);
+#pragma unroll
+    for (int g = 0; g < G; g++) {
+        Real P[G];
+        legendre<Real, G>(Real(GL<G>::x(g)), P);
+        Real wv = Real(GL<G>::w(g)) * v[g];
+#pragma unroll
+        for (int n = 0; n < G; n++) c[n] += wv * P[n];
+    }
+#pragma unroll
+    for (int n = 0; n < G; n++) c[n] *= Real(2 * n + 1) * Real(0.5);
+}
+
+// int_s^1 of the interpolant (Legendre coefficients c) and its value at s.
+// The interpolant has degree G-1, so the G-point Gauss rule on [s, 1] gives its
+// integral exactly, with no cancellation as s -> 1.
+template <typename Real, int G>
+OOTS_HD __forceinline__ Real leg_eval(const Real *c, Real t)
+{
+    Real P[G];
+    legendre<Real, G>(t, P);
+    Real v = Real(0);
+#pragma unroll
+    for (int n = 0; n < G; n++) v += c[n] * P[n];
+    return v;
+}
+
+template <typename Real, int G>
+OOTS_HD __forceinline__ void leg_tail(const Real *c, Real s, Real *integral, Real *value)
+{
+    const Real hw = Real(0.5) * (Real(1) - s), mid = Real(0.5) * (Real(1) + s);
+    Real I = Real(0);
+#pragma unroll
+    for (int g = 0; g < G; g++) I += Real(GL<G>::w(g)) * leg_eval<Real, G>(c, mid + hw * Real(GL<G>::x(g)));
+    *integral = hw * I;
+    *value = leg_eval<Real, G>(c, s);
+}
+
+// Everything the integrator needs about one cell.
+template <typename Real> struct CellODE {
+    int ns;
+    Real c;                      // alpha n
+    Real b0;                     // sigma0 n ds of the source traced by A1 (0: not needed)
+    SrcRate<Real> *r;            // ns entries
+    const DevTable<Real> *tabs;  // table of every tabulated source
+};
+
+template <typename Real> struct IntResult {
+    Real x;      // x(h)
+    Real IR;     // int_0^h c (1-x)^2 dt: recombinations per H atom
+    Real lnfav;  // ln <exp(-b0 x)> over the step
+};
+
+// F(x) and F'(x)
+template <typename Real>
+OOTS_HD void ode_F(const CellODE<Real> &C, Real x, Real *F, Real *dF)
+{
+    Real s = Real(0), d = Real(0);
+    for (int i = 0; i < C.ns; i++) {
+        const SrcRate<Real> &r = C.r[i];
+        if (!(r.A > Real(0))) continue;
+        if (r.tab < 0) {
+            Real e = m_expm1(-r.b * x);          // e^{-bx} - 1
+            s += -r.A * e;
+            d += r.A * r.b * (Real(1) + e);
+        } else {
+            const DevTable<Real> &T = C.tabs[r.tab];
+            Real dl = tab_dlnp(T, r.Nin, r.b * x);
+            s += -r.A * r.p * m_expm1(dl);
+            Real px = r.p * m_exp(dl);            // P(Nin + b x)/Q
+            if (px > Real(0)) d += -r.A * px * r.b * tab_dlnp_dN(T, r.Nin + r.b * x);
+        }
+    }
+    *F = s;
+    *dF = d;
+}
+
+// Per-source values at the root, used by the secant slope:
+//   lne = ln of the transmitted fraction at the root (monochromatic: -b xe;
+//   tabulated: ln(P(Ne)/Q)), Ne = entry column + b xe (tabulated only).
+template <typename Real> struct SrcEq { Real lne; Real Ne; };
+
+// D = (F(xe + d) - F(xe))/d + c (2 (1 - xe) - d), d != 0, from difference
+// forms that keep full relative precision for small |d| and cannot overflow
+// for large |d| (every product below is a transmitted fraction <= 1).
+template <typename Real>
+OOTS_HD Real ode_D(const CellODE<Real> &C, const SrcEq<Real> *Q, Real xe, Real d)
+{
+    Real s = Real(0);
+    for (int i = 0; i < C.ns; i++) {
+        const SrcRate<Real> &r = C.r[i];
+        if (!(r.A > Real(0))) continue;
+        if (r.tab < 0) {
+            Real bd = r.b * d;
+            if (bd > Real(-20)) s += r.A * m_exp(Q[i].lne) * (-m_expm1(-bd));
+            else s += r.A * (m_exp(Q[i].lne) - m_exp(Q[i].lne - bd));
+        } else {
+            const DevTable<Real> &T = C.tabs[r.tab];
+            if (d > Real(0)) {
+                Real dl = tab_dlnp(T, Q[i].Ne, r.b * d);                 // ln P(Ne + b d) - ln P(Ne)
+                s += r.A * m_exp(Q[i].lne) * (-m_expm1(dl));
+            } else {
+                Real dl = tab_dlnp(T, Q[i].Ne + r.b * d, -r.b * d);      // ln P(Ne) - ln P(Ne + b d)
+                s += -r.A * m_exp(Q[i].lne - dl) * (-m_expm1(dl));       // -(P(Ne+bd) - P(Ne))/Q
+            }
+        }
+    }
+    return s / d + C.c * (Real(2) * (Real(1) - xe) - d);
+}
+
+template <typename Real> struct IntCfg;
+template <> struct IntCfg<double> {
+    enum { G = 8 };
+    static OOTS_HD double umax() { return 40.0; }
+    static OOTS_HD double tolq() { return 1e-14; }
+};
+template <> struct IntCfg<float> {
+    enum { G = 4 };
+    static OOTS_HD float umax() { return 20.0f; }
+    static OOTS_HD float tolq() { return 2e-7f; }
+};
+
+template <typename Real>
+OOTS_HD Real attenuation_average(const CellODE<Real> &C, const SrcEq<Real> *Q, Real xe, Real d0, Real Dinf,
+                                 Real h, Real ustar, Real ut, bool in_panels, Real wt);
+
+// Integrate one cell from x0 over h.  sigma0 scales the tabulated b (= n ds)
+// to an optical depth for the curvature scale.
+template <typename Real>
+OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, Real sigma0)
+{
+    constexpr int G = IntCfg<Real>::G;
+    IntResult<Real> R;
+    R.x = x0;
+    R.IR = Real(0);
+    R.lnfav = -C.b0 * x0;
+    if (!(h > Real(0))) return R;
+
+    // photon-free cell: du/dt = -c u^2, u = 1 - x (closed form)
+    bool lit = false;
+    for (int i = 0; i < C.ns; i++) lit |= (C.r[i].A > Real(0));
+    if (!lit) {
+        Real u0 = Real(1) - x0;
+        Real u = u0 / (Real(1) + C.c * u0 * h);
+        R.x = Real(1) - u;
+        R.IR = u0 - u;
+        if (C.b0 > Real(0)) {
+            // x rises monotonically from x0: average exp(-b0 (x(t) - x0)) by
+            // Gauss-Legendre in t on the closed-form trajectory
+            Real acc = Real(0);
+#pragma unroll
+            for (int g = 0; g < G; g++) {
+                Real t = Real(0.5) * h * (Real(1) + Real(GL<G>::x(g)));
+                Real ut = u0 / (Real(1) + C.c * u0 * t);
+                acc += Real(GL<G>::w(g)) * Real(0.5) * m_exp(-C.b0 * (u0 - ut));
+            }
+            R.lnfav = -C.b0 * x0 + m_log(acc);
+        }
+        return R;
+    }
+
+    Real F0, dF0;
+    ode_F(C, x0, &F0, &dF0);
+    Real f0 = -F0 + C.c * (Real(1) - x0) * (Real(1) - x0);
+    if (f0 == Real(0)) {
+        R.IR = h * C.c * (Real(1) - x0) * (Real(1) - x0);
+        return R;
+    }
+
+    // root: Newton from the left of the root (f convex, decreasing)
+    Real xe;
+    {
+        Real xl = f0 > Real(0) ? x0 : Real(0);
+        Real fl;
+        if (f0 > Real(0)) fl = f0;
+        else { Real Fz, dFz; ode_F(C, Real(0), &Fz, &dFz); fl = -Fz + C.c; }
+        if (!(fl > Real(0))) xe = xl;                    // c = 0: root at 0
+        else {
+            for (int it = 0; it < 80; it++) {
+                Real Fx, dFx;
+                ode_F(C, xl, &Fx, &dFx);
+                Real fx = -Fx + C.c * (Real(1) - xl) * (Real(1) - xl);
+                Real dfx = -dFx - Real(2) * C.c * (Real(1) - xl);
+                if (!(fx > Real(0)) || !(dfx < Real(0))) break;
+                Real xn = xl - fx / dfx;
+                if (xn > Real(1)) xn = Real(1);
+                if (!(xn > xl)) break;
+                bool done = (xn - xl) <= Real(4) * RealLimits<Real>::eps() * xn;
+                xl = xn;
+                if (done) break;
+            }
+            xe = xl;
+        }
+    }
+    Real d0 = x0 - xe;
+    if (d0 == Real(0)) {
+        R.IR = h * C.c * (Real(1) - x0) * (Real(1) - x0);
+        return R;
+    }
+
+    // per-source values at the root and the slope at the root
+    SrcEq<Real> Q[MAX_SRC];
+    Real bmax = Real(0);
+    Real Dinf = Real(2) * C.c * (Real(1) - xe);
+    for (int i = 0; i < C.ns; i++) {
+        const SrcRate<Real> &r = C.r[i];
+        Q[i].lne = -RealLimits<Real>::inf();
+        Q[i].Ne = Real(0);
+        if (!(r.A > Real(0))) continue;
+        if (r.tab < 0) {
+            Q[i].lne = -r.b * xe;
+            Dinf += r.A * r.b * m_exp(Q[i].lne);
+            bmax = m_max(bmax, r.b);
+        } else {
+            const DevTable<Real> &T = C.tabs[r.tab];
+            Q[i].Ne = r.Nin + r.b * xe;
+            Q[i].lne = m_log(r.p) + tab_dlnp(T, r.Nin, r.b * xe);
+            Real pe = m_exp(Q[i].lne);
+            if (pe > Real(0)) Dinf += -r.A * pe * r.b * tab_dlnp_dN(T, Q[i].Ne);
+            bmax = m_max(bmax, sigma0 * r.b);
+        }
+    }
+    Real ad0 = m_abs(d0);
+    // start of the near-equilibrium tail in w = e^u: the secant slope bends on
+    // |d| ~ 1/bmax (photoionisation) and |d| ~ 1 - xe (recombination)
+    Real wt = Real(1);
+    if (bmax * ad0 > Real(0.5)) wt = Real(0.5) / (bmax * ad0);
+    if (Real(0.5) * (Real(1) - xe) < wt * ad0) wt = Real(0.5) * (Real(1) - xe) / ad0;
+    Real ut = m_log(wt);
+    // when the tail would start deeper than umax, |d| is already below the
+    // working precision there: start it at -umax and drop its smooth remainder
+    const bool clamped = ut < -IntCfg<Real>::umax();
+    if (clamped) ut = -IntCfg<Real>::umax();
+
+    Real T = Real(0), IR = Real(0);
+    Real uk = Real(0);
+    bool found = false;
+    Real ustar = Real(0);
+    // adaptive panels in u: a panel is accepted when its Gauss sum agrees with
+    // the sum over its two halves to tolq * h; the halves are then used
+    Real du = Real(1);
+    const Real tolq = IntCfg<Real>::tolq() * h;
+    int npan = 0;
+    while (uk > ut && npan < 400) {
+        Real ua = uk - du;
+        if (ua < ut) ua = ut;
+        Real um = Real(0.5) * (uk + ua);
+        // nodal values of 1/D and c(1-x)^2/D on both halves
+        Real vD[2][G], vR[2][G], Ih[2];
+        for (int hh = 0; hh < 2; hh++) {
+            const Real lo = hh ? ua : um, hi = hh ? um : uk;     // hh = 0: upper half [um, uk]
+            const Real hw = Real(0.5) * (hi - lo), mid = Real(0.5) * (hi + lo);
+            Ih[hh] = Real(0);
+#pragma unroll
+            for (int g = 0; g < G; g++) {
+                Real u = mid + hw * Real(GL<G>::x(g));
+                Real d = d0 * m_exp(u);
+                Real xi = xe + d;
+                Real invD = Real(1) / ode_D(C, Q, xe, d);
+                vD[hh][g] = invD;
+                vR[hh][g] = C.c * (Real(1) - xi) * (Real(1) - xi) * invD;
+                Ih[hh] += Real(GL<G>::w(g)) * hw * invD;
+            }
+        }
+        // the whole panel by one Gauss sum, to estimate the error of the halves
+        Real Ifull = Real(0);
+        {
+            const Real hw = Real(0.5) * (uk - ua), mid = um;
+#pragma unroll
+            for (int g = 0; g < G; g++) {
+                Real u = mid + hw * Real(GL<G>::x(g));
+                Real d = d0 * m_exp(u);
+                Real invD = Real(1) / ode_D(C, Q, xe, d);
+                Ifull += Real(GL<G>::w(g)) * hw * invD;
+            }
+        }
+        npan++;
+        const Real err = m_abs(Ifull - (Ih[0] + Ih[1]));
+        if (err > tolq && (uk - ua) > Real(1e-9)) {
+            du = Real(0.5) * (uk - ua);
+            continue;
+        }
+        // accepted: walk the upper half, then the lower half
+        for (int hh = 0; hh < 2 && !found; hh++) {
+            const Real lo = hh ? ua : um, hi = hh ? um : uk;
+            const Real hw = Real(0.5) * (hi - lo), mid = Real(0.5) * (hi + lo);
+            if (T + Ih[hh] >= h) {
+                // invert within the half: s in [-1, 1] maps to u = mid + hw s;
+                // T(s) = T + hw * int_s^1 (1/D); solve T(s) = h
+                Real cD[G], cR[G];
+                leg_coeffs<Real, G>(vD[hh], cD);
+                leg_coeffs<Real, G>(vR[hh], cR);
+                Real s = Real(1) - Real(2) * (h - T) / Ih[hh];
+                if (s < Real(-1)) s = Real(-1);
+                Real slo = Real(-1), shi = Real(1);
+                for (int it = 0; it < 60; it++) {
+                    Real I, v;
+                    leg_tail<Real, G>(cD, s, &I, &v);
+                    Real g = T + hw * I - h;            // decreasing in s, g(-1) >= 0 > g(1)
+                    if (g == Real(0)) break;
+                    if (g > Real(0)) slo = s; else shi = s;
+                    Real sn = s + g / (hw * v);
+                    if (!(sn > slo && sn < shi)) sn = Real(0.5) * (slo + shi);
+                    if (m_abs(sn - s) <= Real(4) * RealLimits<Real>::eps() || shi - slo <= Real(4) * RealLimits<Real>::eps()) { s = sn; break; }
+                    s = sn;
+                }
+                Real I, v;
+                leg_tail<Real, G>(cR, s, &I, &v);
+                IR += hw * I;
+                ustar = mid + hw * s;
+                found = true;
+            } else {
+                T += Ih[hh];
+                Real sR = Real(0);
+#pragma unroll
+                for (int g = 0; g < G; g++) sR += Real(GL<G>::w(g)) * vR[hh][g];
+                IR += hw * sR;
+            }
+        }
+        if (found) break;
+        du = m_min(Real(1), Real(2) * (uk - ua));
+        uk = ua;
+    }
+    if (!found) {
+        // tail: T(u) = T + (ut - u)/Dinf + Rt(w), Rt(w) = int_w^wt (1/D - 1/Dinf)/w' dw'
+        Real wte = m_exp(ut);
+        Real cR0 = C.c * (Real(1) - xe) * (Real(1) - xe);
+        Real qD[G], qR[G];
+        const bool smooth = !clamped;
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+            Real w = Real(0.5) * wte * (Real(1) + Real(GL<G>::x(g)));
+            Real d = d0 * w;
+            Real xi = xe + d;
+            Real invD = Real(1) / ode_D(C, Q, xe, d);
+            qD[g] = smooth ? (invD - Real(1) / Dinf) / w : Real(0);
+            qR[g] = smooth ? (C.c * (Real(1) - xi) * (Real(1) - xi) * invD - cR0 / Dinf) / w : Real(0);
+        }
+        Real cD[G], cRc[G];
+        leg_coeffs<Real, G>(qD, cD);
+        leg_coeffs<Real, G>(qR, cRc);
+        // Newton on T(u) = h: T(u) = T + (ut - u)/Dinf + Rt(e^u), dT/du = -1/D(u)
+        // with 1/D = 1/Dinf + w q(w) from the interpolant; bracketed in [ulo, ut]
+        Real u = ut - Dinf * (h - T);
+        Real uhi = ut, ulo = -RealLimits<Real>::inf();
+        for (int it = 0; it < 60; it++) {
+            Real w = m_exp(u);
+            Real s = Real(2) * w / wte - Real(1);
+            if (s < Real(-1)) s = Real(-1);
+            Real I, v;
+            leg_tail<Real, G>(cD, s, &I, &v);
+            Real g = T + (ut - u) / Dinf + Real(0.5) * wte * I - h;   // decreasing in u, g(ut) < 0
+            if (g == Real(0)) break;
+            if (g > Real(0)) ulo = u; else uhi = u;
+            Real invD = Real(1) / Dinf + w * v;
+            Real un = u + g / invD;
+            if (!(un < uhi && un > ulo))
+                un = (ulo > -RealLimits<Real>::inf()) ? Real(0.5) * (ulo + uhi) : u - (uhi - u) - Real(1);
+            bool conv = m_abs(un - u) <= Real(8) * RealLimits<Real>::eps() * (Real(1) + m_abs(u));
+            u = un;
+            if (conv) break;
+        }
+        Real w = m_exp(u);
+        Real s = Real(2) * w / wte - Real(1);
+        if (s < Real(-1)) s = Real(-1);
+        Real I, v;
+        leg_tail<Real, G>(cRc, s, &I, &v);
+        IR += cR0 * (ut - u) / Dinf + Real(0.5) * wte * I;
+        ustar = u;
+    }
+    R.x = xe + d0 * m_exp(ustar);
+    R.IR = IR;
+    if (C.b0 > Real(0)) R.lnfav = attenuation_average(C, Q, xe, d0, Dinf, h, ustar, ut, found, wt);
+    return R;
+}
+
+// Second pass for A1 (Eq. 3): <exp(-b0 x)> over the step, once the end point
+// u* is known.  Relative to the trajectory's smallest x the weight
+// exp(-b0 (x - x_min)) is largest at that end and falls monotonically away
+// from it, so the integral is marched from the heavy end with adaptive panels
+// (relative to the sum so far) and stopped where the weight is negligible.
+template <typename Real>
+OOTS_HD Real attenuation_average(const CellODE<Real> &C, const SrcEq<Real> *Q, Real xe, Real d0, Real Dinf,
+                                 Real h, Real ustar, Real ut, bool in_panels, Real wt)
+{
+    constexpr int G = IntCfg<Real>::G;
+    const Real xend = xe + d0 * m_exp(ustar);
+    const Real xmin = m_min(xend, xe + d0);
+    const Real wcut = Real(2) * IntCfg<Real>::umax();      // weight below e^-wcut is dropped
+    Real S = Real(0), T2 = Real(0);   // weighted and unweighted time on the same nodes
+    // tail part [u*, ut] (near-equilibrium: the weight varies by at most e^0.5 there)
+    Real ustart = ustar;
+    if (!in_panels) {
+        const Real wte = m_exp(ut);
+        const Real e0 = m_exp(-C.b0 * (xe - xmin));
+        Real q[G], qt[G];
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+            Real w = Real(0.5) * wte * (Real(1) + Real(GL<G>::x(g)));
+            Real d = d0 * w;
+            Real invD = Real(1) / ode_D(C, Q, xe, d);
+            q[g] = (m_exp(-C.b0 * (xe + d - xmin)) * invD - e0 / Dinf) / w;
+            qt[g] = (invD - Real(1) / Dinf) / w;
+        }
+        Real cq[G], cqt[G];
+        leg_coeffs<Real, G>(q, cq);
+        leg_coeffs<Real, G>(qt, cqt);
+        Real s = Real(2) * m_exp(ustar) / wte - Real(1);
+        if (s < Real(-1)) s = Real(-1);
+        Real I, v;
+        leg_tail<Real, G>(cq, s, &I, &v);
+        S += e0 * (ut - ustar) / Dinf + Real(0.5) * wte * I;
+        leg_tail<Real, G>(cqt, s, &I, &v);
+        T2 += (ut - ustar) / Dinf + Real(0.5) * wte * I;
+        ustart = ut;
+    }
+    // panel part [ustart, 0]: heavy end is u = ustart when x decreases (d0 > 0),
+    // u = 0 when x increases (d0 < 0)
+    const bool up = d0 > Real(0);          // march from ustart upward to 0
+    Real pos = up ? ustart : Real(0);
+    const Real end = up ? Real(0) : ustart;
+    Real du = m_min(Real(1), Real(0.25) / m_max(C.b0 * m_abs(d0) * m_exp(pos), Real(1e-30)));
+    int np = 0;
+    while ((up ? pos < end : pos > end) && np < 600) {
+        Real nxt = up ? m_min(pos + du, end) : m_max(pos - du, end);
+        Real lo = m_min(pos, nxt), hi = m_max(pos, nxt);
+        Real mid = Real(0.5) * (lo + hi), hw = Real(0.5) * (hi - lo);
+        Real full = Real(0), halves = Real(0), thalves = Real(0);
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+            Real d = d0 * m_exp(mid + hw * Real(GL<G>::x(g)));
+            full += Real(GL<G>::w(g)) * hw * m_exp(-C.b0 * (xe + d - xmin)) / ode_D(C, Q, xe, d);
+        }
+#pragma unroll
+        for (int hh = 0; hh < 2; hh++) {
+            Real m2 = mid + (hh ? Real(0.5) : Real(-0.5)) * hw;
+#pragma unroll
+            for (int g = 0; g < G; g++) {
+                Real d = d0 * m_exp(m2 + Real(0.5) * hw * Real(GL<G>::x(g)));
+                Real invD = Real(1) / ode_D(C, Q, xe, d);
+                halves += Real(GL<G>::w(g)) * Real(0.5) * hw * m_exp(-C.b0 * (xe + d - xmin)) * invD;
+                thalves += Real(GL<G>::w(g)) * Real(0.5) * hw * invD;
+            }
+        }
+        np++;
+        if (m_abs(full - halves) > IntCfg<Real>::tolq() * Real(10) * (S + halves) && hw > Real(1e-12)) {
+            du = hw;
+            continue;
+        }
+        S += halves;
+        T2 += thalves;
+        pos = nxt;
+        // once the weight is negligible, the rest only adds (unweighted) time
+        Real xp = xe + d0 * m_exp(pos);
+        if (C.b0 * (xp - xmin) > wcut) { T2 = h; break; }
+        du = m_min(Real(1), Real(4) * hw);
+    }
+    Real fav = S / (T2 > Real(0) ? T2 : h);
+    return -C.b0 * xmin + m_log(fav > Real(0) ? fav : RealLimits<Real>::eps());
+}
+
+// dx/dt at x
+template <typename Real>
+OOTS_HD __forceinline__ Real ode_rhs(const CellODE<Real> &C, Real x)
+{
+    Real F, dF;
+    ode_F(C, x, &F, &dF);
+    return -F + C.c * (Real(1) - x) * (Real(1) - x);
+}
+
+} // namespace oots

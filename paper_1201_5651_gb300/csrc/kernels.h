@@ -1,0 +1,53 @@
+// Kernel launch interfaces used by the host driver.
+#pragma once
+#include <cuda_runtime.h>
+#include "oots_internal.h"
+
+namespace oots {
+
+template <typename Real> struct DevTable;
+struct ff;
+template <typename Real> struct ColT;
+
+// Tile shapes of the wavefront sweep: (id, TX, TY, TZ); one thread per (j,k) column.
+#define OOTS_SHAPES(X) \
+    X(0, 16, 8, 8)     \
+    X(1, 32, 8, 8)     \
+    X(2, 16, 16, 16)   \
+    X(3, 32, 16, 16)   \
+    X(4, 8, 8, 8)      \
+    X(5, 32, 4, 4)
+enum { NUM_SHAPES = 6 };
+static const int SHAPE_DIMS[NUM_SHAPES][3] = {{16, 8, 8}, {32, 8, 8}, {16, 16, 16}, {32, 16, 16}, {8, 8, 8}, {32, 4, 4}};
+
+template <typename Real> struct SweepParams {
+    const GridDev<Real> *grids;
+    const Job *jobs;
+    const TileItem *items;
+    int nitems;
+    int which;                         // 0: trace x into N1; 1: trace xh into N2
+    unsigned *ticket;                  // zeroed before each launch
+    unsigned *flags;                   // one per tile, zeroed before each launch
+    void *faceN_raw;                   // per tile 3 faces x FMAX columns
+    Real *faceW;                       // per tile 3 faces x FMAX weight factors
+    const DevTable<Real> *tabs;
+    int *err;                          // sticky device error
+    long long spin_limit;              // bounded wait on upstream tiles
+    long long skip_publish;            // tile that never publishes (fault-injection test), -1: none
+};
+
+template <typename Real> cudaError_t prepare_sweeps();
+template <typename Real> int sweep_occupancy(int shape, int mode);   // resident CTAs per SM
+template <typename Real> bool sweep_shape_ok(int shape);              // fits the shared memory of this device
+template <typename Real>
+cudaError_t launch_sweep(const SweepParams<Real> &P, int shape, int mode, int nblocks, cudaStream_t s);
+
+// Per-cell passes
+enum { OP_RATEDT = 0, OP_HALF = 1, OP_FULL1 = 2, OP_FULL2 = 3 };
+template <typename Real>
+cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
+                        const DevTable<Real> *tabs, int op, int nsm, cudaStream_t s);
+template <typename Real>
+cudaError_t launch_finalize(const GridDev<Real> *grids, int ngrid, int stage, cudaStream_t s);
+
+} // namespace oots

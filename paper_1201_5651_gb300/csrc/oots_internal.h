@@ -1,0 +1,66 @@
+// Internal types shared by the host driver and the CUDA kernels.
+#pragma once
+#include <stdint.h>
+
+namespace oots {
+
+enum { MAX_SRC = 64 };          // sources per grid
+
+// Device-side error codes written to DevState::err (first one sticks).
+enum { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1, DEVERR_BOUNDS = 2 };
+
+// One (grid, source, octant) sweep: the octant of cells on one side of the
+// source vertex along each axis, traced outward from the vertex (Sect. 5).
+struct Job {
+    int grid;              // index into the launch's grid array
+    int src;               // source index within the grid
+    int v[3];              // source vertex
+    int sg[3];             // octant signs (+1 / -1)
+    int ext[3];            // octant extent in cells
+    int off[3];            // tile offset: octant-local i of tile I starts at I*T - off
+    int nt[3];             // tiles per axis
+    long long tile_base;   // index of tile (0,0,0) in the flag and face arrays
+};
+
+// One tile of a job, ordered in the work list by tile diagonal I+J+K.
+struct TileItem { int job; unsigned short I, J, K, pad; };
+
+// Per-grid state that lives on the device, read and written by the kernels
+// (so that substeps can be replayed from a CUDA graph without host sync).
+struct DevState {
+    double t, t_end;          // current time, end of the advance
+    double dt;                // timestep of the substep in flight (0: done)
+    double dt_fixed;          // > 0: fixed timestep
+    double K1, K3, K4;        // Eq. 4 factors (<= 0: off)
+    unsigned long long dt_bits;   // min over cells of the criterion (bits of a positive double)
+    double sumQ;              // sum of the source rates [1/s]
+    double bud_step[4];       // emitted, absorbed, new ions, recombinations of the last substep
+    double bud_total[4];      // accumulated since the last reset
+    double cell_volume;       // dx^3
+    long long nsub;           // substeps taken
+    int done;                 // t >= t_end
+    int err;                  // DEVERR_*
+    int pad[2];
+};
+
+// Description of one grid for the kernels (Real = float or double).
+template <typename Real> struct GridDev {
+    int nx, ny, nz;
+    long long ncell;
+    Real dx;
+    Real sigma0, tau0, alpha;
+    const Real *n;            // density (nullptr: uniform n_uniform)
+    Real n_uniform;
+    const Real *x;            // state the sweep traces / the cell kernels start from
+    const Real *xh;           // half-step state (A3 second sweep input)
+    Real *xout;               // where the cell kernels write
+    Real *N1;                 // entry columns of the first trace, nsrc x ncell
+    Real *N2;                 // entry columns of the second trace, nsrc x ncell
+    int nsrc;
+    int vtx[MAX_SRC][3];
+    Real qfac[MAX_SRC];       // Q / (4 pi dx^3)
+    int tab[MAX_SRC];         // -1 monochromatic, else table index
+    DevState *st;
+};
+
+} // namespace oots
