@@ -164,6 +164,24 @@ int oots_step(oots_ctx *ctx, double dt);
  * receive the final time and the number of substeps taken by this call. */
 int oots_advance(oots_ctx *ctx, double t_end, double *t_out, long long *nsub_out);
 
+/* Enqueue exactly n substeps toward t_end on the context's stream (graph
+ * replays, dt kept on the device; substeps after t_end is reached do no work)
+ * and return without waiting.  Pair with oots_synchronize. */
+int oots_run_substeps(oots_ctx *ctx, long long n, double t_end);
+
+/* Run one substep eagerly with a CUDA event around every kernel launch and
+ * report, for each launch in order, its kind (OOTS_K_* below) and duration
+ * in milliseconds.  nmax: capacity of kinds/ms; *n_out: launches reported. */
+#define OOTS_K_SWEEP1    1   /* first trace (columns of x^n)             */
+#define OOTS_K_RATEDT    2   /* Eq. 4 criterion, minimum over cells      */
+#define OOTS_K_FINAL0    3   /* choose dt                                */
+#define OOTS_K_HALF      4   /* half-step integration (A3)               */
+#define OOTS_K_SWEEP2    5   /* second trace on the half-step state (A3) */
+#define OOTS_K_FULL      6   /* full-step integration and photon budget  */
+#define OOTS_K_FINAL1    7   /* close the substep                        */
+#define OOTS_K_IMPLICIT  8   /* implicit sweep (A1)                      */
+int oots_profile_substep(oots_ctx *ctx, int *kinds, double *ms, int nmax, int *n_out);
+
 /* ---- read-back --------------------------------------------------------------------------- */
 
 /* Neutral fraction of every cell (ncell doubles; FP32 state is widened). */

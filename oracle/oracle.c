@@ -478,7 +478,11 @@ static double src_F(const or_srcrate *r, double x)
 static double src_dF(const or_srcrate *r, double xe, double d)
 {
     if (r->A == 0.0 || d == 0.0) return 0.0;
-    if (r->kind == 0) return r->A * exp(-r->b * xe) * (-expm1(-r->b * d));
+    if (r->kind == 0) {
+        /* A (e^{-b xe} - e^{-b (xe + d)}), written so that no factor exceeds 1 */
+        if (d > 0) return r->A * exp(-r->b * xe) * (-expm1(-r->b * d));
+        return -r->A * exp(-r->b * (xe + d)) * (-expm1(r->b * d));
+    }
     double Ne = r->Nin + r->b * xe;
     if (d > 0) {
         double lp = or_tab_lnp(&r->tab, Ne);

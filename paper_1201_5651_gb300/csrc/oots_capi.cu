@@ -51,7 +51,27 @@ struct SourceH {
     double T;
 };
 
+// Optional per-launch timing (oots_profile_substep): events around each launch.
+struct LaunchProfiler {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kinds;
+    cudaStream_t s = nullptr;
+    void mark(int kind)
+    {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        cudaEventRecord(e, s);
+        ev.push_back(e);
+        kinds.push_back(kind);
+    }
+    ~LaunchProfiler()
+    {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+};
+
 struct LaunchSetBase {
+    LaunchProfiler *prof = nullptr;
     virtual ~LaunchSetBase() {}
     virtual int substep(cudaStream_t s, bool fixed_dt) = 0;
     virtual int trace_for_dt(cudaStream_t s) = 0;
@@ -310,19 +330,25 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     {
         if (nitems == 0) return OOTS_OK;
         CU(cudaMemsetAsync(d_sync, 0, sync_bytes, s));
+        if (prof) prof->mark(0);
         CU(launch_sweep<Real>(params(which), shape, mode, mode == 0 ? nblocks0 : nblocks1, s));
+        if (prof) prof->mark(mode == 1 ? OOTS_K_IMPLICIT : (which == 0 ? OOTS_K_SWEEP1 : OOTS_K_SWEEP2));
         return OOTS_OK;
     }
 
     int cell(cudaStream_t s, int op)
     {
+        if (prof) prof->mark(0);
         CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op, 0, s));
+        if (prof) prof->mark(op == OP_RATEDT ? OOTS_K_RATEDT : (op == OP_HALF ? OOTS_K_HALF : OOTS_K_FULL));
         return OOTS_OK;
     }
 
     int fin(cudaStream_t s, int stage)
     {
+        if (prof) prof->mark(0);
         CU(launch_finalize<Real>(d_grids, (int)ctxs.size(), stage, s));
+        if (prof) prof->mark(stage == 0 ? OOTS_K_FINAL0 : OOTS_K_FINAL1);
         return OOTS_OK;
     }
 
@@ -822,6 +848,54 @@ int oots_advance(oots_ctx *c, double t_end, double *t_out, long long *nsub_out)
     }
     if (t_out) *t_out = c->h_st.t;
     if (nsub_out) *nsub_out = c->h_st.nsub - n0;
+    return OOTS_OK;
+}
+
+int oots_run_substeps(oots_ctx *c, long long n, double t_end)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (n < 0 || !std::isfinite(t_end)) return fail(OOTS_E_INVAL, "n %lld, t_end %g", n, t_end);
+    if (c->batched) return fail(OOTS_E_STATE, "context is part of a batch");
+    int rc = prepare(c);
+    if (rc) return rc;
+    if ((rc = pull_state(c))) return rc;
+    c->h_st.t_end = t_end;
+    c->h_st.done = (t_end > c->h_st.t) ? 0 : 1;
+    if ((rc = push_state(c))) return rc;
+    CU(cudaSetDevice(c->device));
+    return n > 0 ? c->solo->graph_replay(c->stream, (int)n) : OOTS_OK;
+}
+
+int oots_profile_substep(oots_ctx *c, int *kinds, double *ms, int nmax, int *n_out)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!kinds || !ms || !n_out || nmax <= 0) return fail(OOTS_E_INVAL, "profile arguments");
+    if (c->batched) return fail(OOTS_E_STATE, "context is part of a batch");
+    int rc = prepare(c);
+    if (rc) return rc;
+    if ((rc = pull_state(c))) return rc;
+    if (!(c->h_st.t_end > c->h_st.t)) c->h_st.t_end = c->h_st.t + 1e300;
+    c->h_st.done = 0;
+    if ((rc = push_state(c))) return rc;
+    CU(cudaSetDevice(c->device));
+    LaunchProfiler P;
+    P.s = c->stream;
+    c->solo->prof = &P;
+    rc = c->solo->substep(c->stream, c->crit.dt_fixed > 0);
+    c->solo->prof = nullptr;
+    if (rc) return rc;
+    CU(cudaStreamSynchronize(c->stream));
+    if ((rc = check_device_error(c))) return rc;
+    int n = 0;
+    for (size_t i = 0; i + 1 < P.ev.size(); i += 2) {
+        if (n >= nmax) break;
+        float t = 0.0f;
+        CU(cudaEventElapsedTime(&t, P.ev[i], P.ev[i + 1]));
+        kinds[n] = P.kinds[i + 1];
+        ms[n] = t;
+        n++;
+    }
+    *n_out = n;
     return OOTS_OK;
 }
 

@@ -37,8 +37,9 @@ EXPORTS = [
     "oots_get_column_density", "oots_get_budget", "oots_reset_budget", "oots_get_time", "oots_set_time",
     "oots_set_neutral_fraction_device", "oots_get_neutral_fraction_device", "oots_synchronize",
     "oots_batch_create", "oots_batch_advance", "oots_batch_destroy", "oots_set_tile_shape",
-    "oots_tile_shape_info", "oots_debug_set", "oots_version",
+    "oots_tile_shape_info", "oots_debug_set", "oots_version", "oots_run_substeps", "oots_profile_substep",
 ]
+KERNEL_KINDS = {1: "sweep1", 2: "ratedt", 3: "final0", 4: "half", 5: "sweep2", 6: "full", 7: "final1", 8: "implicit"}
 
 
 class OotsError(RuntimeError):
@@ -111,6 +112,8 @@ def load(build_if_missing: bool = True):
         "oots_tile_shape_info": ([ip, P(ip)], ip),
         "oots_debug_set": ([vp, ip, ctypes.c_longlong], ip),
         "oots_version": ([], ctypes.c_char_p),
+        "oots_run_substeps": ([vp, ctypes.c_longlong, dp], ip),
+        "oots_profile_substep": ([vp, P(ip), P(dp), ip, P(ip)], ip),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -245,6 +248,18 @@ class Context:
 
     def synchronize(self):
         return self._c(self.lib.oots_synchronize(self.h))
+
+    def run_substeps(self, n: int, t_end: float):
+        """Enqueue exactly n substeps (asynchronous; pair with synchronize())."""
+        return self._c(self.lib.oots_run_substeps(self.h, int(n), float(t_end)))
+
+    def profile_substep(self):
+        """One eager substep; returns [(kernel kind, milliseconds)] per launch."""
+        kinds = (ctypes.c_int * 32)()
+        ms = (ctypes.c_double * 32)()
+        n = ctypes.c_int()
+        self._c(self.lib.oots_profile_substep(self.h, kinds, ms, 32, ctypes.byref(n)))
+        return [(KERNEL_KINDS.get(kinds[i], str(kinds[i])), ms[i]) for i in range(n.value)]
 
     def reset_error(self):
         return self._c(self.lib.oots_reset_error(self.h))

@@ -53,6 +53,18 @@ def test_recombination_only_closed_form(c, x0, h):
     assert abs(IR - (xr - x0)) <= 1e-13
 
 
+@pytest.mark.parametrize("b", [600.0, 1e4])
+def test_shadowed_opaque_cell_recombines(b):
+    """A very opaque cell behind a huge column (rate ~1e-260) recombines as if
+    unlit: its evolution tends to the A = 0 closed form (no overflow on the way)."""
+    c, x0, h = 1.7e-12, 0.2, 1.9e8
+    u0 = 1.0 - x0
+    xr = 1.0 - u0 / (1.0 + c * u0 * h)
+    x, IF, IR, _ = oracle.integrate(x0, h, c, [(0, 1e-260, b, 0.0)])
+    assert abs(x - xr) <= 1e-14
+    assert abs(IR - (xr - x0)) <= 1e-14
+
+
 def _riccati(G, c, x0, h):
     G, c, x0, h = mp.mpf(G), mp.mpf(c), mp.mpf(x0), mp.mpf(h)
     lam = mp.sqrt(G * G + 4 * c * G)
