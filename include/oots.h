@@ -242,6 +242,38 @@ int oots_tile_shape_info(int shape, int dims[3]);
  * OOTS_E_DEVICE_TIMEOUT without faulting the device. */
 int oots_debug_set(oots_ctx *ctx, int key, long long value);
 
+/* ---- allocation-free trace --------------------------------------------------------------- */
+
+/* The column-density trace of one source, for callers that cannot allocate
+ * device memory -- code that runs inside a CUDA graph capture, inside a
+ * pre-sized memory pool or arena, or in a host process whose allocator must
+ * not be re-entered.  No counterpart in the paper: it exposes the library's
+ * wavefront sweep on its own.
+ *
+ * Inputs and outputs are caller-owned device buffers (x-fastest, ncell
+ * values each): x_dev the neutral fraction, n_dev the density (NULL: the
+ * uniform uniform_n), Nin_dev receives the entry column of every cell
+ * [cm^-2] from a source at pos_cells (snapped to a vertex as in
+ * oots_add_source).  precision: OOTS_FP64 (double buffers) or OOTS_MIXED
+ * (float buffers).  The call enqueues on `stream` (NULL: the default stream)
+ * and returns when the trace has finished.
+ *
+ * Nothing is allocated: the scratch (tile work list, tile flags, published
+ * tile faces, descriptors) is one 32 MiB static device array that every GPU
+ * loading the library holds until the process exits.  A grid that needs more
+ * tiles of 16x8x8 cells than fit in it (about 5400 in FP64, 7200 mixed, i.e.
+ * roughly 5 million cells) is rejected with OOTS_E_INVAL, *status_detail
+ * (optional) set to the tiles needed and the limit in oots_last_error.
+ * The first call on a device sets that device up (looks up the scratch's
+ * device address and opts the kernel into its shared memory): make the first
+ * call before any stream capture.  All calls share the one scratch array and
+ * leave it holding the last call's contents; calls that overlap on the GPU
+ * (different streams or threads at the same time) race and must not be made.
+ * Returns OOTS_OK, OOTS_E_INVAL, OOTS_E_CUDA or OOTS_E_DEVICE_TIMEOUT. */
+int oots_trace_noalloc(int device, int precision, int nx, int ny, int nz, double dx_cm,
+                       const void *n_dev, double uniform_n, const void *x_dev, const double pos_cells[3],
+                       double sigma0, double tau0, void *Nin_dev, void *stream, int *status_detail);
+
 /* Library version string. */
 const char *oots_version(void);
 

@@ -34,6 +34,8 @@ static int fail(int code, const char *fmt, ...)
     return code;
 }
 
+void oots_set_error_text(const char *msg) { g_err = msg; }
+
 #define CU(call)                                                                                   \
     do {                                                                                           \
         cudaError_t e_ = (call);                                                                   \

@@ -38,6 +38,7 @@ EXPORTS = [
     "oots_set_neutral_fraction_device", "oots_get_neutral_fraction_device", "oots_synchronize",
     "oots_batch_create", "oots_batch_advance", "oots_batch_destroy", "oots_set_tile_shape",
     "oots_tile_shape_info", "oots_debug_set", "oots_version", "oots_run_substeps", "oots_profile_substep",
+    "oots_trace_noalloc",
 ]
 KERNEL_KINDS = {1: "sweep1", 2: "ratedt", 3: "final0", 4: "half", 5: "sweep2", 6: "full", 7: "final1", 8: "implicit"}
 
@@ -114,6 +115,7 @@ def load(build_if_missing: bool = True):
         "oots_version": ([], ctypes.c_char_p),
         "oots_run_substeps": ([vp, ctypes.c_longlong, dp], ip),
         "oots_profile_substep": ([vp, P(ip), P(dp), ip, P(ip)], ip),
+        "oots_trace_noalloc": ([ip, ip, ip, ip, ip, dp, vp, dp, vp, P(dp), dp, dp, vp, vp, P(ip)], ip),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -152,6 +154,21 @@ def oots_dtcrit_preset(id: int, scheme: int) -> dtcrit:
     c = dtcrit()
     _check(load().oots_dtcrit_preset(id, scheme, ctypes.byref(c)))
     return c
+
+
+def oots_trace_noalloc(device: int, precision: int, nx: int, ny: int, nz: int, dx: float, n_ptr, uniform_n: float,
+                       x_ptr: int, pos, sigma0: float, tau0: float, nin_ptr: int, stream_ptr=None):
+    """Column trace into caller-owned device buffers without any allocation
+    (pointers are device addresses, e.g. torch tensors' data_ptr())."""
+    p = (ctypes.c_double * 3)(*[float(v) for v in pos])
+    detail = ctypes.c_int(0)
+    rc = load().oots_trace_noalloc(int(device), int(precision), int(nx), int(ny), int(nz), float(dx),
+                                   ctypes.c_void_p(n_ptr) if n_ptr else None, float(uniform_n), ctypes.c_void_p(x_ptr),
+                                   p, float(sigma0), float(tau0), ctypes.c_void_p(nin_ptr),
+                                   ctypes.c_void_p(stream_ptr) if stream_ptr else None, ctypes.byref(detail))
+    if rc != OOTS_OK:
+        raise OotsError(rc, load().oots_last_error(None).decode() + f" (detail {detail.value})")
+    return rc
 
 
 def oots_tile_shape_info(shape: int):
