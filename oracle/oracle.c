@@ -534,8 +534,26 @@ static double cell_D(const or_cell *C, double xe, double d)
         }
         return s + 2.0 * C->c * (1.0 - xe);
     }
-    for (int i = 0; i < C->ns; i++) s += src_dF(&C->r[i], xe, d);
-    return s / d + C->c * (2.0 * (1.0 - xe) - d);
+    if (fabs(d) < 1e-250) return cell_D(C, xe, 0.0);   /* the limit, before anything underflows */
+    for (int i = 0; i < C->ns; i++) {
+        const or_srcrate *r = &C->r[i];
+        if (r->A == 0.0) continue;
+        if (r->kind == 0) {
+            /* (F(xe + d) - F(xe))/d = A b e^{-b xe} (1 - e^{-z})/z, z = b d: the ratio
+             * is formed before the products so that it cannot underflow */
+            double z = r->b * d;
+            if (z > -20.0) {
+                double q = (z != 0.0) ? -expm1(-z) / z : 1.0;
+                s += r->A * r->b * exp(-r->b * xe) * q;
+            } else {
+                /* far below the root: the two transmitted fractions directly */
+                s += r->A * (exp(-r->b * xe) - exp(-r->b * (xe + d))) / d;
+            }
+        } else {
+            s += src_dF(r, xe, d) / d;
+        }
+    }
+    return s + C->c * (2.0 * (1.0 - xe) - d);
 }
 
 /* Root of the (strictly decreasing) right-hand side on [0,1] by bisection. */

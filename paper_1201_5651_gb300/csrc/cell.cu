@@ -20,11 +20,11 @@ __device__ __forceinline__ int find_grid(const long long *off, int ngrid, long l
 }
 
 // Rate parameters of every source for the cell at global index g = (X,Y,Z).
-template <typename Real>
+template <typename Real, int NSMAX>
 __device__ __forceinline__ int cell_rates(const GridDev<Real> &G, const Real *Ncol, const DevTable<Real> *tabs,
                                           int X, int Y, int Z, long long g, Real n, SrcRate<Real> *r)
 {
-    for (int s = 0; s < G.nsrc; s++) {
+    for (int s = 0; s < NSMAX && s < G.nsrc; s++) {
         const int i = X >= G.vtx[s][0] ? X - G.vtx[s][0] : G.vtx[s][0] - 1 - X;
         const int j = Y >= G.vtx[s][1] ? Y - G.vtx[s][1] : G.vtx[s][1] - 1 - Y;
         const int k = Z >= G.vtx[s][2] ? Z - G.vtx[s][2] : G.vtx[s][2] - 1 - Z;
@@ -62,7 +62,7 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     return s;
 }
 
-template <typename Real, int OP>
+template <typename Real, int OP, int NSMAX>
 __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, int ngrid, const long long *offsets,
                                                    long long total, const DevTable<Real> *tabs)
 {
@@ -94,27 +94,27 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
             const int Z = (int)(g / ((long long)G.nx * G.ny));
             const Real n = G.n ? G.n[g] : G.n_uniform;
             const Real x0 = G.x[g];
-            SrcRate<Real> r[MAX_SRC];
+            SrcRate<Real> r[NSMAX];
             const Real *Ncol = (OP == OP_FULL2) ? G.N2 : G.N1;
             CellODE<Real> C;
-            C.ns = cell_rates(G, Ncol, tabs, X, Y, Z, g, n, r);
+            C.ns = cell_rates<Real, NSMAX>(G, Ncol, tabs, X, Y, Z, g, n, r);
             C.c = G.alpha * n;
             C.b0 = Real(0);
             C.r = r;
             C.tabs = tabs;
             if (OP == OP_RATEDT) {
                 // Eq. 4 with T fixed: K1 t_rec, K3 max(0.05, x)/|dx/dt|, K4/|dx/dt|
-                const double xd = fabs((double)ode_rhs(C, x0));
+                const double xd = fabs((double)ode_rhs<Real, NSMAX>(C, x0));
                 if (st->K1 > 0) dtmin = fmin(dtmin, st->K1 / (double(G.alpha) * double(n)));
                 if (xd > 0) {
                     if (st->K3 > 0) dtmin = fmin(dtmin, st->K3 * fmax(0.05, (double)x0) / xd);
                     if (st->K4 > 0) dtmin = fmin(dtmin, st->K4 / xd);
                 }
             } else if (OP == OP_HALF) {
-                IntResult<Real> R = integrate_cell<Real>(C, x0, Real(0.5 * dtd), G.sigma0);
+                IntResult<Real> R = integrate_cell<Real, NSMAX>(C, x0, Real(0.5 * dtd), G.sigma0);
                 const_cast<Real *>(G.xh)[g] = R.x;
             } else {
-                IntResult<Real> R = integrate_cell<Real>(C, x0, Real(dtd), G.sigma0);
+                IntResult<Real> R = integrate_cell<Real, NSMAX>(C, x0, Real(dtd), G.sigma0);
                 G.xout[g] = R.x;
                 const double nV = double(n) * st->cell_volume;
                 ions = nV * (double(x0) - double(R.x));
@@ -177,22 +177,31 @@ __global__ void finalize_kernel(const GridDev<Real> *grids, int ngrid, int stage
     }
 }
 
-template <typename Real>
-cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
-                        const DevTable<Real> *tabs, int op, int nsm, cudaStream_t s)
+template <typename Real, int NSMAX>
+static cudaError_t launch_cell_ns(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
+                                  const DevTable<Real> *tabs, int op, cudaStream_t s)
 {
-    (void)nsm;
-    if (total <= 0) return cudaSuccess;
     const int bs = 256;
     const long long nb = (total + bs - 1) / bs;
     switch (op) {
-    case OP_RATEDT: cell_kernel<Real, OP_RATEDT><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs); break;
-    case OP_HALF: cell_kernel<Real, OP_HALF><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs); break;
-    case OP_FULL1: cell_kernel<Real, OP_FULL1><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs); break;
-    case OP_FULL2: cell_kernel<Real, OP_FULL2><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs); break;
+    case OP_RATEDT: cell_kernel<Real, OP_RATEDT, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs); break;
+    case OP_HALF: cell_kernel<Real, OP_HALF, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs); break;
+    case OP_FULL1: cell_kernel<Real, OP_FULL1, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs); break;
+    case OP_FULL2: cell_kernel<Real, OP_FULL2, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+// nsmax: the largest source count of the grids in the call (1 selects the
+// single-source kernels, whose per-source state stays in registers)
+template <typename Real>
+cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
+                        const DevTable<Real> *tabs, int op, int nsmax, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    if (nsmax <= 1) return launch_cell_ns<Real, 1>(grids, ngrid, offsets, total, tabs, op, s);
+    return launch_cell_ns<Real, MAX_SRC>(grids, ngrid, offsets, total, tabs, op, s);
 }
 
 template <typename Real>

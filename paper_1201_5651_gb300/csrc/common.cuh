@@ -108,10 +108,12 @@ template <typename Real> struct RealLimits;
 template <> struct RealLimits<double> {
     static OOTS_HD __forceinline__ double eps() { return 2.220446049250313e-16; }
     static OOTS_HD __forceinline__ double inf() { return HUGE_VAL; }
+    static OOTS_HD __forceinline__ double tiny() { return 1e-300; }
 };
 template <> struct RealLimits<float> {
     static OOTS_HD __forceinline__ float eps() { return 1.1920929e-07f; }
     static OOTS_HD __forceinline__ float inf() { return HUGE_VALF; }
+    static OOTS_HD __forceinline__ float tiny() { return 1e-37f; }
 };
 
 // ---------------------------------------------------------------------------

@@ -24,28 +24,25 @@
 
 namespace oots {
 
-// Gauss-Legendre rules on [-1, 1] and Legendre polynomials at their nodes.
+// Gauss-Legendre rules on [-1, 1] (nodes and weights in the working precision).
 template <int G> struct GL;
 template <> struct GL<4> {
-    static OOTS_HD __forceinline__ double x(int i) {
-        const double v[4] = {-0.8611363115940526, -0.3399810435848563, 0.3399810435848563, 0.8611363115940526};
-        return v[i];
+    template <typename Real> static OOTS_HD __forceinline__ Real x(int i) {
+        return i == 0 ? Real(-0.8611363115940526) : i == 1 ? Real(-0.3399810435848563) : i == 2 ? Real(0.3399810435848563) : Real(0.8611363115940526);
     }
-    static OOTS_HD __forceinline__ double w(int i) {
-        const double v[4] = {0.3478548451374538, 0.6521451548625461, 0.6521451548625461, 0.3478548451374538};
-        return v[i];
+    template <typename Real> static OOTS_HD __forceinline__ Real w(int i) {
+        return (i == 0 || i == 3) ? Real(0.3478548451374538) : Real(0.6521451548625461);
     }
 };
 template <> struct GL<8> {
-    static OOTS_HD __forceinline__ double x(int i) {
-        const double v[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290, -0.1834346424956498,
-                             0.1834346424956498, 0.5255324099163290, 0.7966664774136267, 0.9602898564975363};
-        return v[i];
+    template <typename Real> static OOTS_HD __forceinline__ Real x(int i) {
+        return i == 0 ? Real(-0.9602898564975363) : i == 1 ? Real(-0.7966664774136267) : i == 2 ? Real(-0.5255324099163290)
+             : i == 3 ? Real(-0.1834346424956498) : i == 4 ? Real(0.1834346424956498) : i == 5 ? Real(0.5255324099163290)
+             : i == 6 ? Real(0.7966664774136267) : Real(0.9602898564975363);
     }
-    static OOTS_HD __forceinline__ double w(int i) {
-        const double v[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873, 0.3626837833783620,
-                             0.3626837833783620, 0.3137066458778873, 0.2223810344533745, 0.1012285362903763};
-        return v[i];
+    template <typename Real> static OOTS_HD __forceinline__ Real w(int i) {
+        return (i == 0 || i == 7) ? Real(0.1012285362903763) : (i == 1 || i == 6) ? Real(0.2223810344533745)
+             : (i == 2 || i == 5) ? Real(0.3137066458778873) : Real(0.3626837833783620);
     }
 };
 
@@ -68,8 +65,8 @@ OOTS_HD __forceinline__ void leg_coeffs(const Real *v, Real *c)
 #pragma unroll
     for (int g = 0; g < G; g++) {
         Real P[G];
-        legendre<Real, G>(Real(GL<G>::x(g)), P);
-        Real wv = Real(GL<G>::w(g)) * v[g];
+        legendre<Real, G>(GL<G>::template x<Real>(g), P);
+        Real wv = GL<G>::template w<Real>(g) * v[g];
 #pragma unroll
         for (int n = 0; n < G; n++) c[n] += wv * P[n];
     }
@@ -97,7 +94,7 @@ OOTS_HD __forceinline__ void leg_tail(const Real *c, Real s, Real *integral, Rea
     const Real hw = Real(0.5) * (Real(1) - s), mid = Real(0.5) * (Real(1) + s);
     Real I = Real(0);
 #pragma unroll
-    for (int g = 0; g < G; g++) I += Real(GL<G>::w(g)) * leg_eval<Real, G>(c, mid + hw * Real(GL<G>::x(g)));
+    for (int g = 0; g < G; g++) I += GL<G>::template w<Real>(g) * leg_eval<Real, G>(c, mid + hw * GL<G>::template x<Real>(g));
     *integral = hw * I;
     *value = leg_eval<Real, G>(c, s);
 }
@@ -118,11 +115,11 @@ template <typename Real> struct IntResult {
 };
 
 // F(x) and F'(x)
-template <typename Real>
+template <typename Real, int NSMAX = MAX_SRC>
 OOTS_HD void ode_F(const CellODE<Real> &C, Real x, Real *F, Real *dF)
 {
     Real s = Real(0), d = Real(0);
-    for (int i = 0; i < C.ns; i++) {
+    for (int i = 0; i < NSMAX && i < C.ns; i++) {
         const SrcRate<Real> &r = C.r[i];
         if (!(r.A > Real(0))) continue;
         if (r.tab < 0) {
@@ -149,29 +146,40 @@ template <typename Real> struct SrcEq { Real lne; Real Ne; };
 // D = (F(xe + d) - F(xe))/d + c (2 (1 - xe) - d), d != 0, from difference
 // forms that keep full relative precision for small |d| and cannot overflow
 // for large |d| (every product below is a transmitted fraction <= 1).
-template <typename Real>
+template <typename Real, int NSMAX = MAX_SRC>
 OOTS_HD Real ode_D(const CellODE<Real> &C, const SrcEq<Real> *Q, Real xe, Real d)
 {
     Real s = Real(0);
-    for (int i = 0; i < C.ns; i++) {
+    const bool tiny = m_abs(d) < RealLimits<Real>::tiny() * Real(1e10);
+    for (int i = 0; i < NSMAX && i < C.ns; i++) {
         const SrcRate<Real> &r = C.r[i];
         if (!(r.A > Real(0))) continue;
         if (r.tab < 0) {
-            Real bd = r.b * d;
-            if (bd > Real(-20)) s += r.A * m_exp(Q[i].lne) * (-m_expm1(-bd));
-            else s += r.A * (m_exp(Q[i].lne) - m_exp(Q[i].lne - bd));
+            // A b e^{-b xe} (1 - e^{-z})/z, z = b d, the ratio formed first (no underflow)
+            const Real z = r.b * d;
+            if (z > Real(-20)) {
+                const Real q = (z != Real(0) && !tiny) ? -m_expm1(-z) / z : Real(1);
+                s += r.A * r.b * m_exp(Q[i].lne) * q;
+            } else {
+                s += r.A * (m_exp(Q[i].lne) - m_exp(Q[i].lne - z)) / d;
+            }
         } else {
             const DevTable<Real> &T = C.tabs[r.tab];
-            if (d > Real(0)) {
-                Real dl = tab_dlnp(T, Q[i].Ne, r.b * d);                 // ln P(Ne + b d) - ln P(Ne)
-                s += r.A * m_exp(Q[i].lne) * (-m_expm1(dl));
+            Real dl = Real(0);
+            if (!tiny) dl = d > Real(0) ? tab_dlnp(T, Q[i].Ne, r.b * d)              // ln P(Ne + b d) - ln P(Ne)
+                                        : tab_dlnp(T, Q[i].Ne + r.b * d, -r.b * d);  // ln P(Ne) - ln P(Ne + b d)
+            if (dl == Real(0)) {
+                // limit d -> 0: -A b P(Ne)/Q d ln P/dN
+                const Real pe = m_exp(Q[i].lne);
+                if (pe > Real(0)) s += -r.A * pe * r.b * tab_dlnp_dN(T, Q[i].Ne);
+            } else if (d > Real(0)) {
+                s += r.A * m_exp(Q[i].lne) * (-m_expm1(dl)) / d;
             } else {
-                Real dl = tab_dlnp(T, Q[i].Ne + r.b * d, -r.b * d);      // ln P(Ne) - ln P(Ne + b d)
-                s += -r.A * m_exp(Q[i].lne - dl) * (-m_expm1(dl));       // -(P(Ne+bd) - P(Ne))/Q
+                s += -r.A * m_exp(Q[i].lne - dl) * (-m_expm1(dl)) / d;   // -(P(Ne+bd) - P(Ne))/(Q d)
             }
         }
     }
-    return s / d + C.c * (Real(2) * (Real(1) - xe) - d);
+    return s + C.c * (Real(2) * (Real(1) - xe) - d);
 }
 
 template <typename Real> struct IntCfg;
@@ -179,20 +187,22 @@ template <> struct IntCfg<double> {
     enum { G = 8 };
     static OOTS_HD double umax() { return 40.0; }
     static OOTS_HD double tolq() { return 1e-14; }
+    static OOTS_HD double zlin() { return 1e-6; }    // linearised step allowed below this h|f'|
 };
 template <> struct IntCfg<float> {
     enum { G = 4 };
     static OOTS_HD float umax() { return 20.0f; }
     static OOTS_HD float tolq() { return 2e-7f; }
+    static OOTS_HD float zlin() { return 3e-3f; }
 };
 
-template <typename Real>
+template <typename Real, int NSMAX>
 OOTS_HD Real attenuation_average(const CellODE<Real> &C, const SrcEq<Real> *Q, Real xe, Real d0, Real Dinf,
                                  Real h, Real ustar, Real ut, bool in_panels, Real wt);
 
 // Integrate one cell from x0 over h.  sigma0 scales the tabulated b (= n ds)
 // to an optical depth for the curvature scale.
-template <typename Real>
+template <typename Real, int NSMAX = MAX_SRC>
 OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, Real sigma0)
 {
     constexpr int G = IntCfg<Real>::G;
@@ -204,7 +214,7 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
 
     // photon-free cell: du/dt = -c u^2, u = 1 - x (closed form)
     bool lit = false;
-    for (int i = 0; i < C.ns; i++) lit |= (C.r[i].A > Real(0));
+    for (int i = 0; i < NSMAX && i < C.ns; i++) lit |= (C.r[i].A > Real(0));
     if (!lit) {
         Real u0 = Real(1) - x0;
         Real u = u0 / (Real(1) + C.c * u0 * h);
@@ -216,9 +226,9 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
             Real acc = Real(0);
 #pragma unroll
             for (int g = 0; g < G; g++) {
-                Real t = Real(0.5) * h * (Real(1) + Real(GL<G>::x(g)));
+                Real t = Real(0.5) * h * (Real(1) + GL<G>::template x<Real>(g));
                 Real ut = u0 / (Real(1) + C.c * u0 * t);
-                acc += Real(GL<G>::w(g)) * Real(0.5) * m_exp(-C.b0 * (u0 - ut));
+                acc += GL<G>::template w<Real>(g) * Real(0.5) * m_exp(-C.b0 * (u0 - ut));
             }
             R.lnfav = -C.b0 * x0 + m_log(acc);
         }
@@ -226,36 +236,57 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
     }
 
     Real F0, dF0;
-    ode_F(C, x0, &F0, &dF0);
+    ode_F<Real, NSMAX>(C, x0, &F0, &dF0);
     Real f0 = -F0 + C.c * (Real(1) - x0) * (Real(1) - x0);
     if (f0 == Real(0)) {
         R.IR = h * C.c * (Real(1) - x0) * (Real(1) - x0);
         return R;
     }
-
-    // root: Newton from the left of the root (f convex, decreasing)
+    // slow cells: when h |f'| is small and the step moves x by much less than
+    // the scales on which f bends (1/b of every source, and 1 - x for the
+    // recombination term), the linearised solution x0 + f0 (e^{h f'} - 1)/f'
+    // is exact to the working tolerance; IR by the midpoint rule
+    if (C.b0 == Real(0)) {
+        const Real df0 = -dF0 - Real(2) * C.c * (Real(1) - x0);
+        const Real z = h * df0;
+        if (m_abs(z) <= IntCfg<Real>::zlin()) {
+            const Real phi = (m_abs(z) > Real(1e-8)) ? m_expm1(z) / z : Real(1) + Real(0.5) * z;
+            const Real dx = h * f0 * phi;
+            Real bm = Real(0);
+            for (int i = 0; i < NSMAX && i < C.ns; i++)
+                if (C.r[i].A > Real(0)) bm = m_max(bm, C.r[i].tab < 0 ? C.r[i].b : sigma0 * C.r[i].b);
+            const Real adx = m_abs(dx);
+            if (bm * adx <= IntCfg<Real>::zlin() && adx <= IntCfg<Real>::zlin() * (Real(1) - x0 + adx) &&
+                x0 + dx >= Real(0) && x0 + dx <= Real(1)) {
+                R.x = x0 + dx;
+                const Real xm = x0 + Real(0.5) * dx;
+                R.IR = h * C.c * (Real(1) - xm) * (Real(1) - xm);
+                return R;
+            }
+        }
+    }
+    // root of the convex, decreasing right-hand side by Newton from x0: from
+    // the right of the root the first step lands left of it, and from the left
+    // Newton increases monotonically to it; [lo, hi] brackets the root
     Real xe;
     {
-        Real xl = f0 > Real(0) ? x0 : Real(0);
-        Real fl;
-        if (f0 > Real(0)) fl = f0;
-        else { Real Fz, dFz; ode_F(C, Real(0), &Fz, &dFz); fl = -Fz + C.c; }
-        if (!(fl > Real(0))) xe = xl;                    // c = 0: root at 0
-        else {
-            for (int it = 0; it < 80; it++) {
-                Real Fx, dFx;
-                ode_F(C, xl, &Fx, &dFx);
-                Real fx = -Fx + C.c * (Real(1) - xl) * (Real(1) - xl);
-                Real dfx = -dFx - Real(2) * C.c * (Real(1) - xl);
-                if (!(fx > Real(0)) || !(dfx < Real(0))) break;
-                Real xn = xl - fx / dfx;
-                if (xn > Real(1)) xn = Real(1);
-                if (!(xn > xl)) break;
-                bool done = (xn - xl) <= Real(4) * RealLimits<Real>::eps() * xn;
-                xl = xn;
-                if (done) break;
-            }
-            xe = xl;
+        Real lo = f0 > Real(0) ? x0 : Real(0), hi = f0 > Real(0) ? Real(1) : x0;
+        Real xk = x0, fk = f0, dfk = -dF0 - Real(2) * C.c * (Real(1) - x0);
+        xe = x0;
+        for (int it = 0; it < 100; it++) {
+            if (fk == Real(0)) { xe = xk; break; }
+            if (fk > Real(0)) lo = m_max(lo, xk); else hi = m_min(hi, xk);
+            Real xn = (dfk < Real(0)) ? xk - fk / dfk : Real(0.5) * (lo + hi);
+            if (!(xn >= lo && xn <= hi)) xn = Real(0.5) * (lo + hi);
+            const bool done = m_abs(xn - xk) <= Real(4) * RealLimits<Real>::eps() * m_max(xn, RealLimits<Real>::tiny())
+                           || (hi - lo) <= Real(4) * RealLimits<Real>::eps() * m_max(hi, RealLimits<Real>::tiny());
+            xk = xn;
+            Real Fk, dFk;
+            ode_F<Real, NSMAX>(C, xk, &Fk, &dFk);
+            fk = -Fk + C.c * (Real(1) - xk) * (Real(1) - xk);
+            dfk = -dFk - Real(2) * C.c * (Real(1) - xk);
+            xe = xk;
+            if (done) break;
         }
     }
     Real d0 = x0 - xe;
@@ -265,10 +296,10 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
     }
 
     // per-source values at the root and the slope at the root
-    SrcEq<Real> Q[MAX_SRC];
+    SrcEq<Real> Q[NSMAX];
     Real bmax = Real(0);
     Real Dinf = Real(2) * C.c * (Real(1) - xe);
-    for (int i = 0; i < C.ns; i++) {
+    for (int i = 0; i < NSMAX && i < C.ns; i++) {
         const SrcRate<Real> &r = C.r[i];
         Q[i].lne = -RealLimits<Real>::inf();
         Q[i].Ne = Real(0);
@@ -304,7 +335,15 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
     Real ustar = Real(0);
     // adaptive panels in u: a panel is accepted when its Gauss sum agrees with
     // the sum over its two halves to tolq * h; the halves are then used
+    // near u = 0 the rate bends on du ~ 1/(b |d0|) whenever the starting state
+    // lies in a source's thin-to-saturated transition (b x0 < 40): start the
+    // panels at that scale (they double after each accepted panel)
     Real du = Real(1);
+    for (int i = 0; i < NSMAX && i < C.ns; i++) {
+        if (!(C.r[i].A > Real(0))) continue;
+        const Real bi = C.r[i].tab < 0 ? C.r[i].b : sigma0 * C.r[i].b;
+        if (bi * x0 < Real(40) && bi * ad0 > Real(0.25)) du = m_min(du, Real(0.25) / (bi * ad0));
+    }
     const Real tolq = IntCfg<Real>::tolq() * h;
     int npan = 0;
     while (uk > ut && npan < 400) {
@@ -319,13 +358,13 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
             Ih[hh] = Real(0);
 #pragma unroll
             for (int g = 0; g < G; g++) {
-                Real u = mid + hw * Real(GL<G>::x(g));
+                Real u = mid + hw * GL<G>::template x<Real>(g);
                 Real d = d0 * m_exp(u);
                 Real xi = xe + d;
-                Real invD = Real(1) / ode_D(C, Q, xe, d);
+                Real invD = Real(1) / ode_D<Real, NSMAX>(C, Q, xe, d);
                 vD[hh][g] = invD;
                 vR[hh][g] = C.c * (Real(1) - xi) * (Real(1) - xi) * invD;
-                Ih[hh] += Real(GL<G>::w(g)) * hw * invD;
+                Ih[hh] += GL<G>::template w<Real>(g) * hw * invD;
             }
         }
         // the whole panel by one Gauss sum, to estimate the error of the halves
@@ -334,10 +373,10 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
             const Real hw = Real(0.5) * (uk - ua), mid = um;
 #pragma unroll
             for (int g = 0; g < G; g++) {
-                Real u = mid + hw * Real(GL<G>::x(g));
+                Real u = mid + hw * GL<G>::template x<Real>(g);
                 Real d = d0 * m_exp(u);
-                Real invD = Real(1) / ode_D(C, Q, xe, d);
-                Ifull += Real(GL<G>::w(g)) * hw * invD;
+                Real invD = Real(1) / ode_D<Real, NSMAX>(C, Q, xe, d);
+                Ifull += GL<G>::template w<Real>(g) * hw * invD;
             }
         }
         npan++;
@@ -379,7 +418,7 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
                 T += Ih[hh];
                 Real sR = Real(0);
 #pragma unroll
-                for (int g = 0; g < G; g++) sR += Real(GL<G>::w(g)) * vR[hh][g];
+                for (int g = 0; g < G; g++) sR += GL<G>::template w<Real>(g) * vR[hh][g];
                 IR += hw * sR;
             }
         }
@@ -395,10 +434,10 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
         const bool smooth = !clamped;
 #pragma unroll
         for (int g = 0; g < G; g++) {
-            Real w = Real(0.5) * wte * (Real(1) + Real(GL<G>::x(g)));
+            Real w = Real(0.5) * wte * (Real(1) + GL<G>::template x<Real>(g));
             Real d = d0 * w;
             Real xi = xe + d;
-            Real invD = Real(1) / ode_D(C, Q, xe, d);
+            Real invD = Real(1) / ode_D<Real, NSMAX>(C, Q, xe, d);
             qD[g] = smooth ? (invD - Real(1) / Dinf) / w : Real(0);
             qR[g] = smooth ? (C.c * (Real(1) - xi) * (Real(1) - xi) * invD - cR0 / Dinf) / w : Real(0);
         }
@@ -436,7 +475,7 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
     }
     R.x = xe + d0 * m_exp(ustar);
     R.IR = IR;
-    if (C.b0 > Real(0)) R.lnfav = attenuation_average(C, Q, xe, d0, Dinf, h, ustar, ut, found, wt);
+    if (C.b0 > Real(0)) R.lnfav = attenuation_average<Real, NSMAX>(C, Q, xe, d0, Dinf, h, ustar, ut, found, wt);
     return R;
 }
 
@@ -445,7 +484,7 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
 // exp(-b0 (x - x_min)) is largest at that end and falls monotonically away
 // from it, so the integral is marched from the heavy end with adaptive panels
 // (relative to the sum so far) and stopped where the weight is negligible.
-template <typename Real>
+template <typename Real, int NSMAX>
 OOTS_HD Real attenuation_average(const CellODE<Real> &C, const SrcEq<Real> *Q, Real xe, Real d0, Real Dinf,
                                  Real h, Real ustar, Real ut, bool in_panels, Real wt)
 {
@@ -462,9 +501,9 @@ OOTS_HD Real attenuation_average(const CellODE<Real> &C, const SrcEq<Real> *Q, R
         Real q[G], qt[G];
 #pragma unroll
         for (int g = 0; g < G; g++) {
-            Real w = Real(0.5) * wte * (Real(1) + Real(GL<G>::x(g)));
+            Real w = Real(0.5) * wte * (Real(1) + GL<G>::template x<Real>(g));
             Real d = d0 * w;
-            Real invD = Real(1) / ode_D(C, Q, xe, d);
+            Real invD = Real(1) / ode_D<Real, NSMAX>(C, Q, xe, d);
             q[g] = (m_exp(-C.b0 * (xe + d - xmin)) * invD - e0 / Dinf) / w;
             qt[g] = (invD - Real(1) / Dinf) / w;
         }
@@ -494,18 +533,18 @@ OOTS_HD Real attenuation_average(const CellODE<Real> &C, const SrcEq<Real> *Q, R
         Real full = Real(0), halves = Real(0), thalves = Real(0);
 #pragma unroll
         for (int g = 0; g < G; g++) {
-            Real d = d0 * m_exp(mid + hw * Real(GL<G>::x(g)));
-            full += Real(GL<G>::w(g)) * hw * m_exp(-C.b0 * (xe + d - xmin)) / ode_D(C, Q, xe, d);
+            Real d = d0 * m_exp(mid + hw * GL<G>::template x<Real>(g));
+            full += GL<G>::template w<Real>(g) * hw * m_exp(-C.b0 * (xe + d - xmin)) / ode_D<Real, NSMAX>(C, Q, xe, d);
         }
 #pragma unroll
         for (int hh = 0; hh < 2; hh++) {
             Real m2 = mid + (hh ? Real(0.5) : Real(-0.5)) * hw;
 #pragma unroll
             for (int g = 0; g < G; g++) {
-                Real d = d0 * m_exp(m2 + Real(0.5) * hw * Real(GL<G>::x(g)));
-                Real invD = Real(1) / ode_D(C, Q, xe, d);
-                halves += Real(GL<G>::w(g)) * Real(0.5) * hw * m_exp(-C.b0 * (xe + d - xmin)) * invD;
-                thalves += Real(GL<G>::w(g)) * Real(0.5) * hw * invD;
+                Real d = d0 * m_exp(m2 + Real(0.5) * hw * GL<G>::template x<Real>(g));
+                Real invD = Real(1) / ode_D<Real, NSMAX>(C, Q, xe, d);
+                halves += GL<G>::template w<Real>(g) * Real(0.5) * hw * m_exp(-C.b0 * (xe + d - xmin)) * invD;
+                thalves += GL<G>::template w<Real>(g) * Real(0.5) * hw * invD;
             }
         }
         np++;
@@ -526,11 +565,11 @@ OOTS_HD Real attenuation_average(const CellODE<Real> &C, const SrcEq<Real> *Q, R
 }
 
 // dx/dt at x
-template <typename Real>
+template <typename Real, int NSMAX = MAX_SRC>
 OOTS_HD __forceinline__ Real ode_rhs(const CellODE<Real> &C, Real x)
 {
     Real F, dF;
-    ode_F(C, x, &F, &dF);
+    ode_F<Real, NSMAX>(C, x, &F, &dF);
     return -F + C.c * (Real(1) - x) * (Real(1) - x);
 }
 

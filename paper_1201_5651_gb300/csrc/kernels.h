@@ -46,7 +46,7 @@ cudaError_t launch_sweep(const SweepParams<Real> &P, int shape, int mode, int nb
 enum { OP_RATEDT = 0, OP_HALF = 1, OP_FULL1 = 2, OP_FULL2 = 3 };
 template <typename Real>
 cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
-                        const DevTable<Real> *tabs, int op, int nsm, cudaStream_t s);
+                        const DevTable<Real> *tabs, int op, int nsmax, cudaStream_t s);
 template <typename Real>
 cudaError_t launch_finalize(const GridDev<Real> *grids, int ngrid, int stage, cudaStream_t s);
 

@@ -137,6 +137,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     long long *d_offsets = nullptr;
     long long total = 0;
     int nblocks0 = 1, nblocks1 = 1;
+    int nsmax = 1;                     // largest source count among the grids
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     bool graph_fixed = false;
@@ -225,6 +226,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
             G.N1 = (Real *)c->d_N1;
             G.N2 = (Real *)c->d_N2;
             G.nsrc = (int)c->src.size();
+            if (G.nsrc > nsmax) nsmax = G.nsrc;
             G.st = c->d_st;
             for (int s = 0; s < G.nsrc; s++) {
                 const SourceH &S = c->src[s];
@@ -341,7 +343,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     int cell(cudaStream_t s, int op)
     {
         if (prof) prof->mark(0);
-        CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op, 0, s));
+        CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op, nsmax, s));
         if (prof) prof->mark(op == OP_RATEDT ? OOTS_K_RATEDT : (op == OP_HALF ? OOTS_K_HALF : OOTS_K_FULL));
         return OOTS_OK;
     }

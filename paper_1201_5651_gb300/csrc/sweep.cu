@@ -249,7 +249,7 @@ sweep_kernel(SweepParams<Real> P)
                         CellODE<Real> C;
                         C.ns = 1; C.c = G.alpha * n; C.b0 = sig * n * dx * sf; C.r = &r; C.tabs = P.tabs;
                         const Real dt = Real(G.st->dt);
-                        IntResult<Real> R = integrate_cell<Real>(C, sD[e], dt, sig);
+                        IntResult<Real> R = integrate_cell<Real, 1>(C, sD[e], dt, sig);
                         Real dtau_eff = -R.lnfav;
                         if (!(dtau_eff >= Real(0))) dtau_eff = Real(0);
                         sN[hidx(li, lj, lk)] = ColT<Real>::add(Nin, dtau_eff / sig);
