@@ -145,11 +145,19 @@ def run_ours(args, rank, world, local_rank):
     n_oct = 1 if args.workload == "stromgren32" else 8
     big = 1e30
 
+    from paper_1201_5651_gb300 import autotune
+    devname = torch.cuda.get_device_name(dev)
+    tuned = {}
+
     def make(precision):
         c = oots.Context.from_workload(w, precision, device=dev, scheme=oots.OOTS_A3, K4=0.25)
         s = torch.cuda.Stream(device=dev)
         c.set_stream(s.cuda_stream)
         c.advance(args.t0 * w.t_rec)          # untimed: develop the front
+        if args.shape >= 0:
+            c.set_tile_shape(args.shape)
+        else:
+            tuned[precision] = autotune.tune(c, devname, len(w.sources), use_cache=not args.retune)
         return c, s
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")   # 256 MB > L2
@@ -260,7 +268,8 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "f32 (state, rates; float-float columns)", "data": "synthetic (seeded generators)",
         "config": {"workload": args.workload, "describe": _describe(args.workload), "ncell": w.ncell,
                    "nsrc": nsrc, "scheme": "A3", "criterion": "dt02 (K4=1/4)", "precision": "mixed",
-                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}"},
+                   "l2": "flushed (256 MB write) between timed steps", "parallelism": f"replicas x{world}",
+                   "tile_shape": {k: oots.oots_tile_shape_info(v)[1] if v is not None else None for k, v in tuned.items()}},
         "fp64": {"value": value_fp64, "ms_per_step": t_fp64 / k64, "steps": k64},
         "mixed_over_fp64": value / value_fp64,
         "accuracy_vs_fp64": acc,
@@ -336,6 +345,8 @@ def main():
     ap.add_argument("--workload", default="lognormal128_bb")
     ap.add_argument("--t0", type=float, default=0.05)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shape", type=int, default=-1, help="tile shape id (-1: autotuned)")
+    ap.add_argument("--retune", action="store_true", help="ignore the autotuner cache")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

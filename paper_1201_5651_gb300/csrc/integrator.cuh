@@ -256,7 +256,9 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
             for (int i = 0; i < NSMAX && i < C.ns; i++)
                 if (C.r[i].A > Real(0)) bm = m_max(bm, C.r[i].tab < 0 ? C.r[i].b : sigma0 * C.r[i].b);
             const Real adx = m_abs(dx);
-            if (bm * adx <= IntCfg<Real>::zlin() && adx <= IntCfg<Real>::zlin() * (Real(1) - x0 + adx) &&
+            // photoionisation bends on 1/b; the recombination term's curvature 2c
+            // changes the increment by ~ c h dx relative
+            if (bm * adx <= IntCfg<Real>::zlin() && C.c * h * adx <= IntCfg<Real>::zlin() * IntCfg<Real>::zlin() &&
                 x0 + dx >= Real(0) && x0 + dx <= Real(1)) {
                 R.x = x0 + dx;
                 const Real xm = x0 + Real(0.5) * dx;
@@ -318,6 +320,18 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
         }
     }
     Real ad0 = m_abs(d0);
+    // already next to the root (|d0| far below both bending scales): the
+    // linearised solution about x_eq, d(t) = d0 e^{-Dinf t}
+    if (bmax * ad0 <= IntCfg<Real>::zlin() && ad0 <= IntCfg<Real>::zlin() * (Real(1) - xe) && C.b0 == Real(0)) {
+        const Real e = m_exp(-Dinf * h);
+        R.x = xe + d0 * e;
+        const Real one = Real(1) - xe;
+        // int c (1 - xe - d)^2 dt = c one^2 h - 2 c one d0 (1 - e)/Dinf + c d0^2 (1 - e^2)/(2 Dinf)
+        const Real g1 = (Dinf * h > Real(1e-6)) ? -m_expm1(-Dinf * h) / Dinf : h;
+        const Real g2 = (Dinf * h > Real(1e-6)) ? -m_expm1(Real(-2) * Dinf * h) / (Real(2) * Dinf) : h;
+        R.IR = C.c * (one * one * h - Real(2) * one * d0 * g1 + d0 * d0 * g2);
+        return R;
+    }
     // start of the near-equilibrium tail in w = e^u: the secant slope bends on
     // |d| ~ 1/bmax (photoionisation) and |d| ~ 1 - xe (recombination)
     Real wt = Real(1);

@@ -14,11 +14,11 @@ template <typename Real> struct ColT;
     X(0, 16, 8, 8)     \
     X(1, 32, 8, 8)     \
     X(2, 16, 16, 16)   \
-    X(3, 32, 16, 16)   \
+    X(3, 8, 16, 16)    \
     X(4, 8, 8, 8)      \
     X(5, 32, 4, 4)
 enum { NUM_SHAPES = 6 };
-static const int SHAPE_DIMS[NUM_SHAPES][3] = {{16, 8, 8}, {32, 8, 8}, {16, 16, 16}, {32, 16, 16}, {8, 8, 8}, {32, 4, 4}};
+static const int SHAPE_DIMS[NUM_SHAPES][3] = {{16, 8, 8}, {32, 8, 8}, {16, 16, 16}, {8, 16, 16}, {8, 8, 8}, {32, 4, 4}};
 
 template <typename Real> struct SweepParams {
     const GridDev<Real> *grids;

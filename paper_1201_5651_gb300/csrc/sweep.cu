@@ -59,6 +59,9 @@ sweep_kernel(SweepParams<Real> P)
     Real *sW = reinterpret_cast<Real *>(sN + HZ * HY * HX);            // 1/max(dtau, tau0); 0 outside the octant
     Real *sD = sW + HZ * HY * HX;                                      // column increment n x ds (MODE 1: x0)
     Real *sI = sD + NC;                                                // entry column N_in (output)
+    Real *sG1 = sI + NC;                                               // 1-D weight of the t1-1 neighbour
+    Real *sG2 = sG1 + NC;                                              // 1-D weight of the t2-1 neighbour
+    unsigned char *sMode = reinterpret_cast<unsigned char *>(sG2 + NC); // per-cell chain mode (see below)
     __shared__ unsigned s_ticket;
     __shared__ double s_bud[3];
 
@@ -98,7 +101,24 @@ sweep_kernel(SweepParams<Real> P)
             const int li = e % TX, lj = (e / TX) % TY, lk = e / (TX * TY);
             const int i = i0 + li, j = j0 + lj, k = k0 + lk;
             Real dN = Real(0);
+            // chain mode: bits 0-1 dominant axis; bit 2 / bit 3: the t1-1 / t2-1
+            // neighbour exists (inside the octant); bit 4 the vertex cell; bit 5
+            // tied dominant axis (general path); bit 7 outside the octant
+            unsigned char mode = 0x80;
             if (i >= 0 && j >= 0 && k >= 0 && i < J.ext[0] && j < J.ext[1] && k < J.ext[2]) {
+                const int c2i[3] = {2 * i + 1, 2 * j + 1, 2 * k + 1};
+                const int idx3[3] = {i, j, k};
+                const int cmi = max(c2i[0], max(c2i[1], c2i[2]));
+                const int nt = (c2i[0] == cmi) + (c2i[1] == cmi) + (c2i[2] == cmi);
+                if (i + j + k == 0) mode = 0x10;
+                else if (nt > 1) mode = 0x20;
+                else {
+                    const int a = c2i[0] == cmi ? 0 : (c2i[1] == cmi ? 1 : 2);
+                    const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+                    mode = (unsigned char)(a | (idx3[t1] > 0 ? 4 : 0) | (idx3[t2] > 0 ? 8 : 0));
+                    sG1[e] = Real(c2i[t1]) / Real(c2i[a]);
+                    sG2[e] = Real(c2i[t2]) / Real(c2i[a]);
+                }
                 const int X = J.sg[0] > 0 ? J.v[0] + i : J.v[0] - 1 - i;
                 const int Y = J.sg[1] > 0 ? J.v[1] + j : J.v[1] - 1 - j;
                 const int Z = J.sg[2] > 0 ? J.v[2] + k : J.v[2] - 1 - k;
@@ -117,6 +137,7 @@ sweep_kernel(SweepParams<Real> P)
                 }
             }
             sD[e] = dN;
+            sMode[e] = mode;
         }
 
         // 2. wait for the face-adjacent upstream tiles
@@ -178,13 +199,33 @@ sweep_kernel(SweepParams<Real> P)
             if (tid < NT && li >= 0 && li < TX) {
                 const int lj = clj, lk = clk;
                 const int i = i0 + li, j = j0 + lj, k = k0 + lk;
-                if (i >= 0 && j >= 0 && k >= 0 && i < J.ext[0] && j < J.ext[1] && k < J.ext[2]) {
+                const int e = (lk * TY + lj) * TX + li;
+                const unsigned mode = sMode[e];
+                if (!(mode & 0x80)) {
                     const int idx[3] = {i, j, k};
                     const int loc[3] = {li, lj, lk};
                     const int c2[3] = {2 * i + 1, 2 * j + 1, 2 * k + 1};
                     const int cm = max(c2[0], max(c2[1], c2[2]));
                     Col Nin = ColT<Real>::zero();
-                    if (i + j + k > 0) {
+                    if (!(mode & 0x30)) {
+                        // one dominant axis a: bilinear weights of the four upwind
+                        // cells times their optical-depth factors, normalised once
+                        const int a = mode & 3;
+                        const int str[3] = {1, HX, HX * HY};
+                        const int s1 = str[a == 2 ? 0 : a + 1], s2 = str[a == 0 ? 2 : a - 1];   // strides of t1, t2
+                        const int h00 = hidx(li, lj, lk) - str[a];
+                        const Real g1 = sG1[e], g2 = sG2[e];
+                        const Real w00 = (Real(1) - g1) * (Real(1) - g2) * sW[h00];
+                        const Real w01 = (mode & 8) ? (Real(1) - g1) * g2 * sW[h00 - s2] : Real(0);
+                        const Real w10 = (mode & 4) ? g1 * (Real(1) - g2) * sW[h00 - s1] : Real(0);
+                        const Real w11 = ((mode & 12) == 12) ? g1 * g2 * sW[h00 - s1 - s2] : Real(0);
+                        const Real r = Real(1) / (w00 + w01 + w10 + w11);
+                        Col acc = ColT<Real>::fma_w(ColT<Real>::zero(), w00 * r, sN[h00]);
+                        if (mode & 8) acc = ColT<Real>::fma_w(acc, w01 * r, sN[h00 - s2]);
+                        if (mode & 4) acc = ColT<Real>::fma_w(acc, w10 * r, sN[h00 - s1]);
+                        if ((mode & 12) == 12) acc = ColT<Real>::fma_w(acc, w11 * r, sN[h00 - s1 - s2]);
+                        Nin = acc;
+                    } else if (mode & 0x20) {
                         Col sum = ColT<Real>::zero();
                         int ntied = 0;
 #pragma unroll
@@ -216,7 +257,6 @@ sweep_kernel(SweepParams<Real> P)
                         }
                         Nin = ColT<Real>::div(sum, Real(ntied));
                     }
-                    const int e = (lk * TY + lj) * TX + li;
                     const Real nin_r = ColT<Real>::to_real(Nin);
                     sI[e] = nin_r;
                     if (MODE == 0) {
@@ -336,7 +376,7 @@ template <typename Real, int TX, int TY, int TZ>
 constexpr size_t sweep_smem()
 {
     return (size_t)(TX + 1) * (TY + 1) * (TZ + 1) * (sizeof(typename ColT<Real>::type) + sizeof(Real))
-         + (size_t)2 * TX * TY * TZ * sizeof(Real);
+         + (size_t)4 * TX * TY * TZ * sizeof(Real) + (size_t)TX * TY * TZ;
 }
 
 template <typename Real, int TX, int TY, int TZ, int MODE>
