@@ -113,6 +113,22 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_max(v, world, device):
+    """Maximum of one float over all ranks (the slowest rank sets the job time)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, t_ms):
+    """Whole-job throughput: the units all ranks processed over the max-over-ranks time."""
+    return world * units_per_rank / (t_ms / 1e3)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -185,12 +201,7 @@ def run_ours(args, rank, world, local_rank):
         return tot
 
     def dist_max(v):
-        if world == 1:
-            return v
-        import torch.distributed as tdist
-        t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{dev}")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(v, world, f"cuda:{dev}")
 
     def barrier():
         if world > 1:
@@ -207,7 +218,7 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     barrier()
     t_mixed = dist_max(t_mixed)
-    value = world * w.ncell * args.steps / (t_mixed / 1e3)
+    value = job_rate(w.ncell * args.steps, world, t_mixed)
 
     # per-kernel durations of one substep (eager, events around every launch)
     prof = {}
@@ -226,7 +237,7 @@ def run_ours(args, rank, world, local_rank):
     cf, sf_ = make("fp64")
     k64 = max(3, min(args.steps, 10))
     t_fp64 = dist_max(timed(cf, sf_, k64, 1))
-    value_fp64 = world * w.ncell * k64 / (t_fp64 / 1e3)
+    value_fp64 = job_rate(w.ncell * k64, world, t_fp64)
 
     # ---------------- accuracy of mixed vs FP64 at a common time ----------------
     tm, _ = cm.get_time()
@@ -257,7 +268,7 @@ def run_ours(args, rank, world, local_rank):
             host_out.copy_(dbuf, non_blocking=True)
         sm_.synchronize()
     t_e2e = dist_max(time.perf_counter() - t0)
-    e2e = {"value": world * w.ncell * ke / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 4 * w.ncell,
+    e2e = {"value": job_rate(w.ncell * ke, world, t_e2e * 1e3), "unit": UNIT, "h2d_bytes_per_step": 4 * w.ncell,
            "d2h_bytes_per_step": 4 * w.ncell}
 
     if rank != 0:

@@ -236,10 +236,12 @@ int oots_set_tile_shape(oots_ctx *ctx, int shape);
 /* Number of tile shapes and the dimensions of one. */
 int oots_tile_shape_info(int shape, int dims[3]);
 
-/* Debug controls for tests: key 1 = spin limit of the bounded tile waits
- * (iterations, > 0); key 2 = index of a tile that never publishes its faces
- * (-1 = none), which makes its downstream waits run out and the call return
- * OOTS_E_DEVICE_TIMEOUT without faulting the device. */
+/* Debug and tuning controls: key 1 = spin limit of the bounded tile waits
+ * (iterations, > 0); key 2 = index of a tile that never publishes its
+ * progress (-1 = none), which makes its downstream waits run out and the call
+ * return OOTS_E_DEVICE_TIMEOUT without faulting the device; key 3 = planes a
+ * sweep tile completes between two progress publications (1..64; 0 = the
+ * default of 4).  OOTS_E_INVAL for an unknown key or a value out of range. */
 int oots_debug_set(oots_ctx *ctx, int key, long long value);
 
 /* ---- allocation-free trace --------------------------------------------------------------- */

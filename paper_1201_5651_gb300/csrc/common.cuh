@@ -73,6 +73,7 @@ template <> struct ColT<double> {
     static OOTS_HD __forceinline__ double add(double a, double d) { return a + d; }
     static OOTS_HD __forceinline__ double addc(double a, double b) { return a + b; }
     static OOTS_HD __forceinline__ double to_real(double a) { return a; }
+    static OOTS_HD __forceinline__ double sub_r(double a, double b) { return a - b; }
 };
 template <> struct ColT<float> {
     typedef ff type;
@@ -82,6 +83,8 @@ template <> struct ColT<float> {
     static OOTS_HD __forceinline__ ff add(ff a, float d) { return ff_add_f(a, d); }
     static OOTS_HD __forceinline__ ff addc(ff a, ff b) { return ff_add(a, b); }
     static OOTS_HD __forceinline__ float to_real(ff a) { return a.hi + a.lo; }
+    // a - b rounded to one float (exact high-part difference for close columns)
+    static OOTS_HD __forceinline__ float sub_r(ff a, ff b) { return (a.hi - b.hi) + (a.lo - b.lo); }
 };
 
 // ---------------------------------------------------------------------------

@@ -9,16 +9,17 @@ template <typename Real> struct DevTable;
 struct ff;
 template <typename Real> struct ColT;
 
-// Tile shapes of the wavefront sweep: (id, TX, TY, TZ); one thread per (j,k) column.
+// Tile shapes of the wavefront sweep: (id, TX, TY, TZ); one chain thread per
+// (j,k) column (TY*TZ a multiple of 32) plus one producer warp.
 #define OOTS_SHAPES(X) \
     X(0, 16, 8, 8)     \
     X(1, 32, 8, 8)     \
     X(2, 16, 16, 16)   \
     X(3, 8, 16, 16)    \
     X(4, 8, 8, 8)      \
-    X(5, 32, 4, 4)
+    X(5, 16, 16, 8)
 enum { NUM_SHAPES = 6 };
-static const int SHAPE_DIMS[NUM_SHAPES][3] = {{16, 8, 8}, {32, 8, 8}, {16, 16, 16}, {8, 16, 16}, {8, 8, 8}, {32, 4, 4}};
+static const int SHAPE_DIMS[NUM_SHAPES][3] = {{16, 8, 8}, {32, 8, 8}, {16, 16, 16}, {8, 16, 16}, {8, 8, 8}, {16, 16, 8}};
 
 template <typename Real> struct SweepParams {
     const GridDev<Real> *grids;
@@ -34,6 +35,7 @@ template <typename Real> struct SweepParams {
     int *err;                          // sticky device error
     long long spin_limit;              // bounded wait on upstream tiles
     long long skip_publish;            // tile that never publishes (fault-injection test), -1: none
+    int chunk;                         // planes per published progress step (<= 0: 4)
 };
 
 template <typename Real> cudaError_t prepare_sweeps();

@@ -95,6 +95,7 @@ struct oots_ctx {
     int shape = -1;
     long long spin_limit = 1ll << 22;
     long long skip_publish = -1;
+    int sweep_chunk = 0;               // planes per progress step of the sweep (0: default)
     size_t rsize = 8;
     void *d_x = nullptr, *d_n = nullptr, *d_xh = nullptr, *d_N1 = nullptr, *d_N2 = nullptr;
     int nsrc_alloc = 0;
@@ -143,6 +144,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     bool graph_fixed = false;
     int *d_err = nullptr;
     long long spin_limit = 1ll << 22, skip_publish = -1;
+    int sweep_chunk = 0;
 
     ~LaunchSet() override
     {
@@ -198,6 +200,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         d_err = c0->d_err;
         spin_limit = c0->spin_limit;
         skip_publish = c0->skip_publish;
+        sweep_chunk = c0->sweep_chunk;
         const int TX = SHAPE_DIMS[shape][0], TY = SHAPE_DIMS[shape][1], TZ = SHAPE_DIMS[shape][2];
         const int T3[3] = {TX, TY, TZ};
         const int FMAX = std::max(TY * TZ, std::max(TX * TZ, TX * TY));
@@ -327,6 +330,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         P.err = d_err;
         P.spin_limit = spin_limit;
         P.skip_publish = skip_publish;
+        P.chunk = sweep_chunk;
         return P;
     }
 
@@ -1030,6 +1034,9 @@ int oots_debug_set(oots_ctx *c, int key, long long value)
         c->spin_limit = value;
     } else if (key == 2) {
         c->skip_publish = value;
+    } else if (key == 3) {
+        if (value < 0 || value > 64) return fail(OOTS_E_INVAL, "sweep chunk %lld", value);
+        c->sweep_chunk = (int)value;
     } else {
         return fail(OOTS_E_INVAL, "debug key %d", key);
     }

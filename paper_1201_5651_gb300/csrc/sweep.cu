@@ -7,19 +7,27 @@
 // the call.  The octants are cut into tiles of TX x TY x TZ cells aligned to
 // global multiples of the tile size (coalesced rows).  Tiles are handed out by
 // an atomic ticket in order of their tile diagonal I+J+K, so every upstream
-// tile was claimed by a running CTA before any tile that waits for it.  A CTA
-//   1. loads its cells' x and n (before waiting: this overlaps the wait) and
-//      forms each cell's column increment n x ds and weight factor
-//      1/max(dtau, tau0);
-//   2. waits (bounded spin, acquire) for the three face-adjacent upstream
-//      tiles; edge and corner neighbours are complete by transitivity;
-//   3. gathers its one-cell halo from their published faces;
-//   4. runs the plane-by-plane recurrence i+j+k = m in shared memory, one
-//      thread per (j, k) column of the tile;
-//   5. publishes its three downstream faces (release) and then writes the
-//      entry columns of its cells to global memory.
-// The recurrence is linear in the columns with weights fixed by the state, so
-// only the weighted sum and one add sit on the critical path of a plane.
+// tile was claimed by a running CTA before any tile that waits for it.
+//
+// Inside a tile the cells are processed plane by plane (li+lj+lk = m, one
+// chain thread per (j,k) column).  The tiles are pipelined: a tile publishes
+// a progress count (planes done) after every chunk of planes, and its three
+// downstream faces are written to global memory as their cells complete, so
+// a downstream tile starts as soon as the planes it needs exist instead of
+// after the whole upstream tile.  Plane m of a tile reads the face of its
+// upstream tile along axis a at that tile's plane m + T_a - 1; edge and corner
+// halo cells are covered by transitivity (the face-adjacent upstream tile
+// waited for them before it completed the plane we wait for).
+//
+// Each CTA holds the chain warps and one producer warp.  The producer waits
+// (bounded spin, acquire) for the upstream progress each chunk needs and
+// stages that chunk's halo cells (a compile-time list sorted by the first
+// plane that reads them) from the published faces into shared memory, running
+// ahead of the chain.  The chain warps form each cell's normalised neighbour
+// weights off the critical path (interior cells before the first wait,
+// halo-adjacent cells once their chunk's halo is staged), so a plane costs
+// one weighted difference sum and one column add.  Shared-memory rows are
+// padded so that a plane's cells sit in distinct banks.
 #include "common.cuh"
 #include "integrator.cuh"
 #include "kernels.h"
@@ -36,6 +44,11 @@ __device__ __forceinline__ void st_release(unsigned *p, unsigned v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// barrier among the chain warps only (the producer warp does not take part)
+template <int N> __device__ __forceinline__ void chain_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
+}
 
 template <typename Col> __device__ __forceinline__ Col ld_face(const Col *p);
 template <> __device__ __forceinline__ double ld_face<double>(const double *p) { return __ldcg(p); }
@@ -44,34 +57,176 @@ template <> __device__ __forceinline__ ff ld_face<ff>(const ff *p)
     float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
     return ff{v.x, v.y};
 }
+template <typename Col> __device__ __forceinline__ void st_face(Col *p, Col v);
+template <> __device__ __forceinline__ void st_face<double>(double *p, double v) { __stcg(p, v); }
+template <> __device__ __forceinline__ void st_face<ff>(ff *p, ff v)
+{
+    __stcg(reinterpret_cast<float2 *>(p), make_float2(v.hi, v.lo));
+}
+
+// Shared-memory layout of a sweep tile: a one-cell halo on the three upstream
+// sides, with the row strides padded so that the cells of one plane
+// li+lj+lk = m handled by a warp (lane t: lj = t % TY, lk = t / TY) fall in
+// distinct banks for 4-byte arrays and in distinct bank pairs within each
+// half-warp for 8-byte arrays.  Along a plane the address moves by SY - 1 per
+// lj and by SZ - 1 per lk.
+constexpr bool plane_conflict_free(int a, int b, int TY, int NT)
+{
+    for (int w = 0; w < NT / 32; w++) {
+        bool b32[32] = {}, b16[2][16] = {};
+        for (int l = 0; l < 32; l++) {
+            const int t = 32 * w + l, lj = t % TY, lk = t / TY;
+            const int off = lj * a + lk * b;
+            if (b32[off % 32]) return false;
+            b32[off % 32] = true;
+            if (b16[l / 16][off % 16]) return false;
+            b16[l / 16][off % 16] = true;
+        }
+    }
+    return true;
+}
+constexpr int pick_plane_stride(int SY, int HY, int TY, int NT)
+{
+    for (int s = SY * HY; s < SY * HY + 64; s++)
+        if (plane_conflict_free(SY - 1, s - 1, TY, NT)) return s;
+    return SY * HY;
+}
+
+template <int TX, int TY, int TZ> struct TileLayout {
+    static constexpr int HX = TX + 1, HY = TY + 1, HZ = TZ + 1;
+    static constexpr int NT = TY * TZ;
+    static constexpr int SY = (HX % 2 == 0) ? HX : HX + 1;          // SY - 1 odd
+    static constexpr int SZ = pick_plane_stride(SY, HY, TY, NT);
+    static constexpr int HSZ = HZ * SZ;                               // entries per array
+    static constexpr int NP = TX + TY + TZ - 2;                       // planes of a tile
+    static constexpr int NE = HY * HZ + TX * HZ + TX * TY;            // halo cells
+    static constexpr int FMAX = (TY * TZ > TX * TZ ? (TY * TZ > TX * TY ? TY * TZ : TX * TY)
+                                                   : (TX * TZ > TX * TY ? TX * TZ : TX * TY));
+    static constexpr OOTS_HD int h(int li, int lj, int lk) { return (lk + 1) * SZ + (lj + 1) * SY + (li + 1); }
+    static_assert(HSZ < (1 << 14) && FMAX <= (1 << 12), "halo entry packing");
+};
+
+// The halo cells of a tile sorted by the first plane that reads them (its
+// key): an X-face cell (-1, lj, lk) is first read by plane max(lj,0) +
+// max(lk,0), a Y-face cell (li, -1, lk) by li + max(lk,0), a Z-face cell
+// (li, lj, -1) by li + lj.  Each entry packs the halo index (14 bits), the
+// index within the upstream face (12 bits), the face (2 bits) and the mask of
+// tile steps (-x, -y, -z) from this tile to the tile that published it.
+template <int TX, int TY, int TZ> struct HaloList {
+    unsigned e[TileLayout<TX, TY, TZ>::NE];
+    unsigned short start[TileLayout<TX, TY, TZ>::NP + 1];
+};
+template <int TX, int TY, int TZ>
+constexpr void halo_entry(int q, int &key, unsigned &packed)
+{
+    typedef TileLayout<TX, TY, TZ> L;
+    int li = 0, lj = 0, lk = 0, face = 0, mask = 0, fq = 0;
+    if (q < L::HY * L::HZ) {
+        lj = q % L::HY - 1; lk = q / L::HY - 1; li = -1; face = 0;
+        key = (lj > 0 ? lj : 0) + (lk > 0 ? lk : 0);
+        mask = 1 | (lj < 0 ? 2 : 0) | (lk < 0 ? 4 : 0);
+        fq = (lk < 0 ? TZ - 1 : lk) * TY + (lj < 0 ? TY - 1 : lj);
+    } else if (q < L::HY * L::HZ + TX * L::HZ) {
+        const int r = q - L::HY * L::HZ;
+        li = r % TX; lk = r / TX - 1; lj = -1; face = 1;
+        key = li + (lk > 0 ? lk : 0);
+        mask = 2 | (lk < 0 ? 4 : 0);
+        fq = (lk < 0 ? TZ - 1 : lk) * TX + li;
+    } else {
+        const int r = q - L::HY * L::HZ - TX * L::HZ;
+        li = r % TX; lj = r / TX; lk = -1; face = 2;
+        key = li + lj;
+        mask = 4;
+        fq = lj * TX + li;
+    }
+    packed = (unsigned)L::h(li, lj, lk) | ((unsigned)fq << 14) | ((unsigned)face << 26) | ((unsigned)mask << 28);
+}
+template <int TX, int TY, int TZ>
+constexpr HaloList<TX, TY, TZ> make_halo_list()
+{
+    typedef TileLayout<TX, TY, TZ> L;
+    HaloList<TX, TY, TZ> H{};
+    int cnt[L::NP + 1] = {};
+    for (int q = 0; q < L::NE; q++) {
+        int key = 0; unsigned p = 0;
+        halo_entry<TX, TY, TZ>(q, key, p);
+        cnt[key + 1]++;
+    }
+    for (int k = 0; k < L::NP; k++) cnt[k + 1] += cnt[k];
+    for (int k = 0; k <= L::NP; k++) H.start[k] = (unsigned short)cnt[k];
+    for (int q = 0; q < L::NE; q++) {
+        int key = 0; unsigned p = 0;
+        halo_entry<TX, TY, TZ>(q, key, p);
+        H.e[cnt[key]++] = p;
+    }
+    return H;
+}
+template <int TX, int TY, int TZ>
+__device__ const HaloList<TX, TY, TZ> g_halo_list = make_halo_list<TX, TY, TZ>();
 
 template <typename Real, int TX, int TY, int TZ, int MODE>
-__global__ void __launch_bounds__(TY *TZ)
+__global__ void __launch_bounds__(TY *TZ + 32)
 sweep_kernel(SweepParams<Real> P)
 {
     typedef typename ColT<Real>::type Col;
-    constexpr int HX = TX + 1, HY = TY + 1, HZ = TZ + 1;
-    constexpr int NT = TY * TZ;
+    typedef TileLayout<TX, TY, TZ> L;
+    constexpr int NT = L::NT;                    // chain threads
     constexpr int NC = TX * TY * TZ;
-    constexpr int FMAX = (TY * TZ > TX * TZ ? (TY * TZ > TX * TY ? TY * TZ : TX * TY) : (TX * TZ > TX * TY ? TX * TZ : TX * TY));
+    constexpr int NP = L::NP;
+    constexpr int FMAX = L::FMAX;
+    constexpr int HSZ = L::HSZ;
+    constexpr int SY = L::SY, SZ = L::SZ;
+    static_assert(NT % 32 == 0, "the chain threads fill whole warps");
+    static_assert(NC % (4 * NT) == 0, "pre-pass batches of four cells per thread");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Col *sN = reinterpret_cast<Col *>(smem_raw);                       // N_out, halo-indexed
-    Real *sW = reinterpret_cast<Real *>(sN + HZ * HY * HX);            // 1/max(dtau, tau0); 0 outside the octant
-    Real *sD = sW + HZ * HY * HX;                                      // column increment n x ds (MODE 1: x0)
-    Real *sI = sD + NC;                                                // entry column N_in (output)
-    Real *sG1 = sI + NC;                                               // 1-D weight of the t1-1 neighbour
-    Real *sG2 = sG1 + NC;                                              // 1-D weight of the t2-1 neighbour
-    unsigned char *sMode = reinterpret_cast<unsigned char *>(sG2 + NC); // per-cell chain mode (see below)
+    // every array is indexed by the padded halo index L::h(li, lj, lk)
+    Col *sN = reinterpret_cast<Col *>(smem_raw);       // N_out of the cell
+    Real *sW = reinterpret_cast<Real *>(sN + HSZ);     // 1/max(dtau, tau0); 0 outside the octant
+    Real *sDI = sW + HSZ;                              // increment n x ds (MODE 1: x0), then N_in
+    Real *sQ = sDI + HSZ;                              // 3 x HSZ neighbour weights (see below)
+    unsigned char *sMode = reinterpret_cast<unsigned char *>(sQ + 3 * HSZ); // chain mode (see below)
     __shared__ unsigned s_ticket;
+    __shared__ volatile int s_ready;             // chunks whose halo is staged
     __shared__ double s_bud[3];
+    const HaloList<TX, TY, TZ> &HL = g_halo_list<TX, TY, TZ>;
 
     Col *const faceN = reinterpret_cast<Col *>(P.faceN_raw);
     const int tid = threadIdx.x;
-    const int clj = tid % TY, clk = tid / TY;
+    const int clj = tid % TY, clk = tid / TY;    // chain threads: own (j,k) column
+    const int chunk = P.chunk > 0 ? P.chunk : 4;
     double bud_ions = 0.0, bud_rec = 0.0;
     int bud_grid = -1;
 
-    auto hidx = [](int li, int lj, int lk) { return ((lk + 1) * HY + (lj + 1)) * HX + (li + 1); };
+    // halo-index strides of the dominant axis a and of its two transverse axes
+    auto str_a = [](int a) { return a == 0 ? 1 : (a == 1 ? SY : SZ); };
+    auto str_t1 = [](int a) { return a == 0 ? SY : (a == 1 ? SZ : 1); };
+    auto str_t2 = [](int a) { return a == 0 ? SZ : (a == 1 ? 1 : SY); };
+
+    // Normalised weights of the (t1-1), (t2-1) and (t1-1,t2-1) upwind
+    // neighbours relative to the (0,0) one, from the 1-D weights g1, g2 held
+    // in sQ[h], sQ[HSZ+h] and the neighbours' optical-depth factors:
+    // N_in = N00 + q01 (N01 - N00) + q10 (N10 - N00) + q11 (N11 - N00).
+    auto weights = [&](int h, unsigned mode) {
+        const int a = mode & 3;
+        const int h00 = h - str_a(a), s1 = str_t1(a), s2 = str_t2(a);
+        const Real g1 = sQ[h], g2 = sQ[HSZ + h];
+        const Real w00 = (Real(1) - g1) * (Real(1) - g2) * sW[h00];
+        const Real w01 = (mode & 8) ? (Real(1) - g1) * g2 * sW[h00 - s2] : Real(0);
+        const Real w10 = (mode & 4) ? g1 * (Real(1) - g2) * sW[h00 - s1] : Real(0);
+        const Real w11 = ((mode & 12) == 12) ? g1 * g2 * sW[h00 - s1 - s2] : Real(0);
+        const Real r = Real(1) / (w00 + w01 + w10 + w11);
+        sQ[h] = w01 * r;
+        sQ[HSZ + h] = w10 * r;
+        sQ[2 * HSZ + h] = w11 * r;
+    };
+    // a regular cell one of whose upwind neighbours lies in the halo
+    auto on_halo = [](int li, int lj, int lk, unsigned mode) {
+        const int a = mode & 3;
+        const int la = a == 0 ? li : (a == 1 ? lj : lk);
+        const int l1 = a == 0 ? lj : (a == 1 ? lk : li);
+        const int l2 = a == 0 ? lk : (a == 1 ? li : lj);
+        return la == 0 || ((mode & 4) && l1 == 0) || ((mode & 8) && l2 == 0);
+    };
 
     for (;;) {
         if (tid == 0) {
@@ -80,6 +235,7 @@ sweep_kernel(SweepParams<Real> P)
             // tiles skip, so no wait is left pending)
             if (t < (unsigned)P.nitems && P.grids[P.jobs[P.items[t].job].grid].st->done) t |= 0x80000000u;
             s_ticket = t;
+            s_ready = 0;
         }
         __syncthreads();
         const unsigned tk = s_ticket;
@@ -94,247 +250,311 @@ sweep_kernel(SweepParams<Real> P)
         const Real *xin = (P.which == 1) ? G.xh : G.x;
         const Real dx = G.dx, sig = G.sigma0, tau0 = G.tau0;
 
-        // 1. own cells: increments and weight factors (halo entries zeroed)
-        for (int e = tid; e < HZ * HY * HX; e += NT) { sW[e] = Real(0); sN[e] = ColT<Real>::zero(); }
-        __syncthreads();
-        for (int e = tid; e < NC; e += NT) {
-            const int li = e % TX, lj = (e / TX) % TY, lk = e / (TX * TY);
-            const int i = i0 + li, j = j0 + lj, k = k0 + lk;
-            Real dN = Real(0);
-            // chain mode: bits 0-1 dominant axis; bit 2 / bit 3: the t1-1 / t2-1
-            // neighbour exists (inside the octant); bit 4 the vertex cell; bit 5
-            // tied dominant axis (general path); bit 7 outside the octant
-            unsigned char mode = 0x80;
-            if (i >= 0 && j >= 0 && k >= 0 && i < J.ext[0] && j < J.ext[1] && k < J.ext[2]) {
-                const int c2i[3] = {2 * i + 1, 2 * j + 1, 2 * k + 1};
-                const int idx3[3] = {i, j, k};
-                const int cmi = max(c2i[0], max(c2i[1], c2i[2]));
-                const int nt = (c2i[0] == cmi) + (c2i[1] == cmi) + (c2i[2] == cmi);
-                if (i + j + k == 0) mode = 0x10;
-                else if (nt > 1) mode = 0x20;
-                else {
-                    const int a = c2i[0] == cmi ? 0 : (c2i[1] == cmi ? 1 : 2);
-                    const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
-                    mode = (unsigned char)(a | (idx3[t1] > 0 ? 4 : 0) | (idx3[t2] > 0 ? 8 : 0));
-                    sG1[e] = Real(c2i[t1]) / Real(c2i[a]);
-                    sG2[e] = Real(c2i[t2]) / Real(c2i[a]);
-                }
-                const int X = J.sg[0] > 0 ? J.v[0] + i : J.v[0] - 1 - i;
-                const int Y = J.sg[1] > 0 ? J.v[1] + j : J.v[1] - 1 - j;
-                const int Z = J.sg[2] > 0 ? J.v[2] + k : J.v[2] - 1 - k;
-                const long long g = (long long)X + (long long)G.nx * ((long long)Y + (long long)G.ny * Z);
-                const Real n = G.n ? __ldg(G.n + g) : G.n_uniform;
-                const Real xv = __ldg(xin + g);
-                const Real c0 = Real(i) + Real(0.5), c1 = Real(j) + Real(0.5), c2 = Real(k) + Real(0.5);
-                const Real cm = m_max(c0, m_max(c1, c2));
-                const Real ds = dx * m_sqrt(c0 * c0 + c1 * c1 + c2 * c2) / cm;
-                if (MODE == 0) {
-                    dN = n * xv * ds;
-                    sW[hidx(li, lj, lk)] = Real(1) / m_max(sig * dN, tau0);
-                } else {
-                    dN = xv;                               // A1: x0, integrated in the chain
-                    sW[hidx(li, lj, lk)] = Real(1);        // set in the chain
-                }
+        if (tid >= NT) {
+            // ---------------- producer warp ----------------
+            const int lane = tid - NT;
+            // zero the halo (read as absent until staged)
+            for (int q = lane; q < L::NE; q += 32) {
+                const int h = __ldg(&HL.e[q]) & 0x3fffu;
+                sN[h] = ColT<Real>::zero();
+                sW[h] = Real(0);
             }
-            sD[e] = dN;
-            sMode[e] = mode;
-        }
-
-        // 2. wait for the face-adjacent upstream tiles
-        if (tid == 0) {
-            long long up[3];
-            int nup = 0;
-            if (it.I > 0) up[nup++] = tile_self - 1;
-            if (it.J > 0) up[nup++] = tile_self - J.nt[0];
-            if (it.K > 0) up[nup++] = tile_self - (long long)J.nt[0] * J.nt[1];
-            for (int q = 0; q < nup; q++) {
-                long long spins = 0;
-                unsigned ns = 32;
-                while (ld_acquire(P.flags + up[q]) == 0u) {
-                    if (++spins > P.spin_limit) { atomicCAS(P.err, 0, (int)DEVERR_TIMEOUT); break; }
-                    __nanosleep(ns);
-                    if (ns < 1024) ns <<= 1;
-                }
-            }
-        }
-        __syncthreads();
-
-        // 3. halo from the published faces
-        {
+            __syncwarp();
             const long long sx = 1, sy = J.nt[0], sz = (long long)J.nt[0] * J.nt[1];
-            // li = -1 plane (X faces of tiles I-1, with J-1 / K-1 edges)
-            for (int q = tid; q < HY * HZ; q += NT) {
-                const int lj = q % HY - 1, lk = q / HY - 1;
-                if (it.I == 0 || (lj < 0 && it.J == 0) || (lk < 0 && it.K == 0)) continue;
-                const long long src = tile_self - sx - (lj < 0 ? sy : 0) - (lk < 0 ? sz : 0);
-                const int fq = (lk < 0 ? TZ - 1 : lk) * TY + (lj < 0 ? TY - 1 : lj);
-                const long long o = src * 3 * FMAX + 0 * FMAX + fq;
-                sN[hidx(-1, lj, lk)] = ld_face<Col>(faceN + o);
-                sW[hidx(-1, lj, lk)] = __ldcg(P.faceW + o);
-            }
-            // lj = -1 plane (Y faces of tiles J-1, with K-1 edge)
-            for (int q = tid; q < TX * HZ; q += NT) {
-                const int li = q % TX, lk = q / TX - 1;
-                if (it.J == 0 || (lk < 0 && it.K == 0)) continue;
-                const long long src = tile_self - sy - (lk < 0 ? sz : 0);
-                const int fq = (lk < 0 ? TZ - 1 : lk) * TX + li;
-                const long long o = src * 3 * FMAX + 1 * FMAX + fq;
-                sN[hidx(li, -1, lk)] = ld_face<Col>(faceN + o);
-                sW[hidx(li, -1, lk)] = __ldcg(P.faceW + o);
-            }
-            // lk = -1 plane (Z face of tile K-1)
-            for (int q = tid; q < TX * TY; q += NT) {
-                const int li = q % TX, lj = q / TX;
-                if (it.K == 0) continue;
-                const long long o = (tile_self - sz) * 3 * FMAX + 2 * FMAX + lj * TX + li;
-                sN[hidx(li, lj, -1)] = ld_face<Col>(faceN + o);
-                sW[hidx(li, lj, -1)] = __ldcg(P.faceW + o);
-            }
-        }
-        __syncthreads();
-
-        // 4. plane-by-plane recurrence
-        for (int m = 0; m < TX + TY + TZ - 2; m++) {
-            const int li = m - clj - clk;
-            if (tid < NT && li >= 0 && li < TX) {
-                const int lj = clj, lk = clk;
-                const int i = i0 + li, j = j0 + lj, k = k0 + lk;
-                const int e = (lk * TY + lj) * TX + li;
-                const unsigned mode = sMode[e];
-                if (!(mode & 0x80)) {
-                    const int idx[3] = {i, j, k};
-                    const int loc[3] = {li, lj, lk};
-                    const int c2[3] = {2 * i + 1, 2 * j + 1, 2 * k + 1};
-                    const int cm = max(c2[0], max(c2[1], c2[2]));
-                    Col Nin = ColT<Real>::zero();
-                    if (!(mode & 0x30)) {
-                        // one dominant axis a: bilinear weights of the four upwind
-                        // cells times their optical-depth factors, normalised once
-                        const int a = mode & 3;
-                        const int str[3] = {1, HX, HX * HY};
-                        const int s1 = str[a == 2 ? 0 : a + 1], s2 = str[a == 0 ? 2 : a - 1];   // strides of t1, t2
-                        const int h00 = hidx(li, lj, lk) - str[a];
-                        const Real g1 = sG1[e], g2 = sG2[e];
-                        const Real w00 = (Real(1) - g1) * (Real(1) - g2) * sW[h00];
-                        const Real w01 = (mode & 8) ? (Real(1) - g1) * g2 * sW[h00 - s2] : Real(0);
-                        const Real w10 = (mode & 4) ? g1 * (Real(1) - g2) * sW[h00 - s1] : Real(0);
-                        const Real w11 = ((mode & 12) == 12) ? g1 * g2 * sW[h00 - s1 - s2] : Real(0);
-                        const Real r = Real(1) / (w00 + w01 + w10 + w11);
-                        Col acc = ColT<Real>::fma_w(ColT<Real>::zero(), w00 * r, sN[h00]);
-                        if (mode & 8) acc = ColT<Real>::fma_w(acc, w01 * r, sN[h00 - s2]);
-                        if (mode & 4) acc = ColT<Real>::fma_w(acc, w10 * r, sN[h00 - s1]);
-                        if ((mode & 12) == 12) acc = ColT<Real>::fma_w(acc, w11 * r, sN[h00 - s1 - s2]);
-                        Nin = acc;
-                    } else if (mode & 0x20) {
-                        Col sum = ColT<Real>::zero();
-                        int ntied = 0;
+            const unsigned have = (it.I > 0 ? 1u : 0u) | (it.J > 0 ? 2u : 0u) | (it.K > 0 ? 4u : 0u);
+            int k = 0;
+            for (int m0 = 0; m0 < NP; m0 += chunk, k++) {
+                const int m1 = min(m0 + chunk, NP);
+                // wait: lane a polls the face-adjacent upstream tile along axis a
+                if (lane < 3 && (have & (1u << lane))) {
+                    const long long up = tile_self - (lane == 0 ? sx : (lane == 1 ? sy : sz));
+                    const unsigned need = (unsigned)min(NP, m1 - 1 + (lane == 0 ? TX : (lane == 1 ? TY : TZ)));
+                    long long spins = 0;
+                    unsigned ns = 32;
+                    while (ld_acquire(P.flags + up) < need) {
+                        if (++spins > P.spin_limit) { atomicCAS(P.err, 0, (int)DEVERR_TIMEOUT); break; }
+                        if ((spins & 31) == 0 && *(volatile int *)P.err != 0) break;   // another tile gave up
+                        __nanosleep(ns);
+                        if (ns < 256) ns <<= 1;
+                    }
+                }
+                __syncwarp();
+                // stage the halo cells first read by planes [m0, m1), four per lane in flight
+                const int b1 = HL.start[m1];
+                for (int base = HL.start[m0] + lane; base < b1; base += 128) {
+                    unsigned en[4];
+                    Col vN[4];
+                    Real vW[4];
 #pragma unroll
-                        for (int a = 0; a < 3; a++) {
-                            if (c2[a] != cm) continue;
-                            ntied++;
+                    for (int u = 0; u < 4; u++) {
+                        const int q = base + 32 * u;
+                        en[u] = q < b1 ? __ldg(&HL.e[q]) : 0u;
+                        const unsigned mask = en[u] >> 28;
+                        if (q < b1 && (mask & ~have) == 0) {
+                            const long long src = tile_self - ((mask & 1) ? sx : 0) - ((mask & 2) ? sy : 0) - ((mask & 4) ? sz : 0);
+                            const long long o = src * 3 * FMAX + (long long)((en[u] >> 26) & 3u) * FMAX + ((en[u] >> 14) & 0xfffu);
+                            vN[u] = ld_face<Col>(faceN + o);
+                            vW[u] = __ldcg(P.faceW + o);
+                        } else {
+                            en[u] = 0u;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        if (en[u]) { sN[en[u] & 0x3fffu] = vN[u]; sW[en[u] & 0x3fffu] = vW[u]; }
+                }
+                __syncwarp();
+                if (lane == 0) { __threadfence_block(); s_ready = k + 1; }
+            }
+        } else {
+            // ---------------- chain warps ----------------
+            // 1. own cells: increments, weight factors, chain modes (loads in
+            //    batches of four cells per thread)
+            for (int e0 = tid; e0 < NC; e0 += 4 * NT) {
+                long long gq[4];
+                bool in[4];
+                Real nv[4], xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int e = e0 + u * NT;
+                    const int li = e % TX, lj = (e / TX) % TY, lk = e / (TX * TY);
+                    const int i = i0 + li, j = j0 + lj, k = k0 + lk;
+                    in[u] = i >= 0 && j >= 0 && k >= 0 && i < J.ext[0] && j < J.ext[1] && k < J.ext[2];
+                    const int X = J.sg[0] > 0 ? J.v[0] + i : J.v[0] - 1 - i;
+                    const int Y = J.sg[1] > 0 ? J.v[1] + j : J.v[1] - 1 - j;
+                    const int Z = J.sg[2] > 0 ? J.v[2] + k : J.v[2] - 1 - k;
+                    gq[u] = (long long)X + (long long)G.nx * ((long long)Y + (long long)G.ny * Z);
+                    nv[u] = in[u] ? (G.n ? __ldg(G.n + gq[u]) : G.n_uniform) : Real(0);
+                    xv[u] = in[u] ? __ldg(xin + gq[u]) : Real(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int e = e0 + u * NT;
+                    const int li = e % TX, lj = (e / TX) % TY, lk = e / (TX * TY);
+                    const int i = i0 + li, j = j0 + lj, k = k0 + lk;
+                    const int h = L::h(li, lj, lk);
+                    Real dN = Real(0), wf = Real(0);
+                    // chain mode: bits 0-1 dominant axis; bit 2 / bit 3: the t1-1 / t2-1
+                    // neighbour exists (inside the octant); bit 4 the vertex cell; bit 5
+                    // tied dominant axis (general path); bit 7 outside the octant
+                    unsigned char mode = 0x80;
+                    if (in[u]) {
+                        const int c2i[3] = {2 * i + 1, 2 * j + 1, 2 * k + 1};
+                        const int idx3[3] = {i, j, k};
+                        const int cmi = max(c2i[0], max(c2i[1], c2i[2]));
+                        const int nt = (c2i[0] == cmi) + (c2i[1] == cmi) + (c2i[2] == cmi);
+                        if (i + j + k == 0) mode = 0x10;
+                        else if (nt > 1) mode = 0x20;
+                        else {
+                            const int a = c2i[0] == cmi ? 0 : (c2i[1] == cmi ? 1 : 2);
                             const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
-                            const Real w1 = Real(c2[t1]) / Real(c2[a]);   // weight of the t1-1 neighbour
-                            const Real w2 = Real(c2[t2]) / Real(c2[a]);
-                            Col acc = ColT<Real>::zero();
-                            Real ws = Real(0);
+                            mode = (unsigned char)(a | (idx3[t1] > 0 ? 4 : 0) | (idx3[t2] > 0 ? 8 : 0));
+                            sQ[h] = Real(c2i[t1]) / Real(c2i[a]);
+                            sQ[HSZ + h] = Real(c2i[t2]) / Real(c2i[a]);
+                        }
+                        const Real c0 = Real(i) + Real(0.5), c1 = Real(j) + Real(0.5), c2 = Real(k) + Real(0.5);
+                        const Real cm = m_max(c0, m_max(c1, c2));
+                        const Real ds = dx * m_sqrt(c0 * c0 + c1 * c1 + c2 * c2) / cm;
+                        if (MODE == 0) {
+                            dN = nv[u] * xv[u] * ds;
+                            wf = Real(1) / m_max(sig * dN, tau0);
+                        } else {
+                            dN = xv[u];                            // A1: x0, integrated in the chain
+                            wf = Real(1);                          // set in the chain
+                        }
+                    }
+                    sN[h] = ColT<Real>::zero();
+                    sW[h] = wf;
+                    sDI[h] = dN;
+                    sMode[h] = mode;
+                }
+            }
+            chain_sync<NT>();
+            // interior cells: neighbour weights before the first wait
+            if (MODE == 0) {
+                for (int li = 0; li < TX; li++) {
+                    const int h = L::h(li, clj, clk);
+                    const unsigned mode = sMode[h];
+                    if (!(mode & 0xB0) && !on_halo(li, clj, clk, mode)) weights(h, mode);
+                }
+            }
+
+            const long long fbase = tile_self * 3 * FMAX;
+            int k = 0;
+            for (int m0 = 0; m0 < NP; m0 += chunk, k++) {
+                const int m1 = min(m0 + chunk, NP);
+                if (tid == 0) {
+                    // the producer always advances (its waits are bounded); this
+                    // bound only guards against a broken invariant
+                    long long spins = 0;
+                    while (s_ready <= k) {
+                        if (++spins > (P.spin_limit << 4)) { atomicCAS(P.err, 0, (int)DEVERR_TIMEOUT); break; }
+                        if ((spins & 255) == 0) __nanosleep(64);
+                    }
+                    __threadfence_block();
+                }
+                chain_sync<NT>();
+                // halo-adjacent cells of this chunk: neighbour weights
+                if (MODE == 0) {
+                    for (int m = m0; m < m1; m++) {
+                        const int li = m - clj - clk;
+                        if (li < 0 || li >= TX) continue;
+                        const int h = L::h(li, clj, clk);
+                        const unsigned mode = sMode[h];
+                        if (!(mode & 0xB0) && on_halo(li, clj, clk, mode)) weights(h, mode);
+                    }
+                }
+                // 2. plane-by-plane recurrence
+                for (int m = m0; m < m1; m++) {
+                    const int li = m - clj - clk;
+                    if (li >= 0 && li < TX) {
+                        const int lj = clj, lk = clk;
+                        const int i = i0 + li, j = j0 + lj, k = k0 + lk;
+                        const int h = L::h(li, lj, lk);
+                        const unsigned mode = sMode[h];
+                        Col Nout = ColT<Real>::zero();
+                        Real wout = Real(0);
+                        if (!(mode & 0x80)) {
+                            wout = sW[h];
+                            const Real dval = sDI[h];
+                            if (MODE == 0 && !(mode & 0x30)) {
+                                // one dominant axis: weighted differences to the (0,0) neighbour
+                                const int a = mode & 3;
+                                const int h00 = h - str_a(a), s1 = str_t1(a), s2 = str_t2(a);
+                                const int h01 = (mode & 8) ? h00 - s2 : h00;
+                                const int h10 = (mode & 4) ? h00 - s1 : h00;
+                                const int h11 = ((mode & 12) == 12) ? h00 - s1 - s2 : h00;
+                                const Col N00 = sN[h00];
+                                const Real d = sQ[h] * ColT<Real>::sub_r(sN[h01], N00)
+                                             + sQ[HSZ + h] * ColT<Real>::sub_r(sN[h10], N00)
+                                             + sQ[2 * HSZ + h] * ColT<Real>::sub_r(sN[h11], N00);
+                                Nout = ColT<Real>::add(N00, d + dval);
+                                sDI[h] = ColT<Real>::to_real(ColT<Real>::add(N00, d));
+                            } else {
+                                Col Nin = ColT<Real>::zero();
+                                if (!(mode & 0x30)) {
+                                    // (MODE 1) one dominant axis: bilinear weights times the
+                                    // neighbours' factors, normalised once
+                                    const int a = mode & 3;
+                                    const int h00 = h - str_a(a), s1 = str_t1(a), s2 = str_t2(a);
+                                    const Real g1 = sQ[h], g2 = sQ[HSZ + h];
+                                    const Real w00 = (Real(1) - g1) * (Real(1) - g2) * sW[h00];
+                                    const Real w01 = (mode & 8) ? (Real(1) - g1) * g2 * sW[h00 - s2] : Real(0);
+                                    const Real w10 = (mode & 4) ? g1 * (Real(1) - g2) * sW[h00 - s1] : Real(0);
+                                    const Real w11 = ((mode & 12) == 12) ? g1 * g2 * sW[h00 - s1 - s2] : Real(0);
+                                    const Real r = Real(1) / (w00 + w01 + w10 + w11);
+                                    Col acc = ColT<Real>::fma_w(ColT<Real>::zero(), w00 * r, sN[h00]);
+                                    if (mode & 8) acc = ColT<Real>::fma_w(acc, w01 * r, sN[h00 - s2]);
+                                    if (mode & 4) acc = ColT<Real>::fma_w(acc, w10 * r, sN[h00 - s1]);
+                                    if ((mode & 12) == 12) acc = ColT<Real>::fma_w(acc, w11 * r, sN[h00 - s1 - s2]);
+                                    Nin = acc;
+                                } else if (mode & 0x20) {
+                                    // tied dominant axes: average of the interpolations along each
+                                    const int idx[3] = {i, j, k};
+                                    const int loc[3] = {li, lj, lk};
+                                    const int c2[3] = {2 * i + 1, 2 * j + 1, 2 * k + 1};
+                                    const int cm = max(c2[0], max(c2[1], c2[2]));
+                                    Col sum = ColT<Real>::zero();
+                                    int ntied = 0;
 #pragma unroll
-                            for (int e1 = 0; e1 < 2; e1++) {
+                                    for (int a = 0; a < 3; a++) {
+                                        if (c2[a] != cm) continue;
+                                        ntied++;
+                                        const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+                                        const Real w1 = Real(c2[t1]) / Real(c2[a]);   // weight of the t1-1 neighbour
+                                        const Real w2 = Real(c2[t2]) / Real(c2[a]);
+                                        Col acc = ColT<Real>::zero();
+                                        Real ws = Real(0);
 #pragma unroll
-                                for (int e2 = 0; e2 < 2; e2++) {
-                                    if (idx[t1] - e1 < 0 || idx[t2] - e2 < 0) continue;
-                                    int nb[3];
-                                    nb[a] = loc[a] - 1;
-                                    nb[t1] = loc[t1] - e1;
-                                    nb[t2] = loc[t2] - e2;
-                                    const int h = hidx(nb[0], nb[1], nb[2]);
-                                    const Real wg = (e1 ? w1 : Real(1) - w1) * (e2 ? w2 : Real(1) - w2);
-                                    const Real w = wg * sW[h];
-                                    acc = ColT<Real>::fma_w(acc, w, sN[h]);
-                                    ws += w;
+                                        for (int e1 = 0; e1 < 2; e1++) {
+#pragma unroll
+                                            for (int e2 = 0; e2 < 2; e2++) {
+                                                if (idx[t1] - e1 < 0 || idx[t2] - e2 < 0) continue;
+                                                int nb[3];
+                                                nb[a] = loc[a] - 1;
+                                                nb[t1] = loc[t1] - e1;
+                                                nb[t2] = loc[t2] - e2;
+                                                const int hn = L::h(nb[0], nb[1], nb[2]);
+                                                const Real wg = (e1 ? w1 : Real(1) - w1) * (e2 ? w2 : Real(1) - w2);
+                                                const Real w = wg * sW[hn];
+                                                acc = ColT<Real>::fma_w(acc, w, sN[hn]);
+                                                ws += w;
+                                            }
+                                        }
+                                        if (ws > Real(0)) sum = ColT<Real>::addc(sum, ColT<Real>::div(acc, ws));
+                                    }
+                                    Nin = ColT<Real>::div(sum, Real(ntied));
+                                }
+                                const Real nin_r = ColT<Real>::to_real(Nin);
+                                sDI[h] = nin_r;
+                                if (MODE == 0) {
+                                    Nout = ColT<Real>::add(Nin, dval);
+                                } else {
+                                    // A1 (Eq. 3): integrate the cell with its entry column
+                                    // frozen; pass on N_in - ln<f>/sigma0
+                                    const int X = J.sg[0] > 0 ? J.v[0] + i : J.v[0] - 1 - i;
+                                    const int Y = J.sg[1] > 0 ? J.v[1] + j : J.v[1] - 1 - j;
+                                    const int Z = J.sg[2] > 0 ? J.v[2] + k : J.v[2] - 1 - k;
+                                    const long long g = (long long)X + (long long)G.nx * ((long long)Y + (long long)G.ny * Z);
+                                    const Real n = G.n ? __ldg(G.n + g) : G.n_uniform;
+                                    const Real c0 = Real(i) + Real(0.5), c1 = Real(j) + Real(0.5), c2r = Real(k) + Real(0.5);
+                                    const Real r2 = c0 * c0 + c1 * c1 + c2r * c2r;
+                                    const Real cmr = m_max(c0, m_max(c1, c2r));
+                                    const Real sf = m_sqrt(r2) / cmr;
+                                    SrcRate<Real> r;
+                                    const int s = J.src;
+                                    r.Nin = nin_r;
+                                    r.tab = G.tab[s];
+                                    if (r.tab < 0) {
+                                        r.A = G.qfac[s] * m_exp(-sig * nin_r) / (n * r2 * sf);
+                                        r.b = sig * n * dx * sf;
+                                        r.p = Real(1);
+                                    } else {
+                                        r.A = G.qfac[s] / (n * r2 * sf);
+                                        r.b = n * dx * sf;
+                                        r.p = m_exp(tab_lnp(P.tabs[r.tab], nin_r));
+                                    }
+                                    CellODE<Real> C;
+                                    C.ns = 1; C.c = G.alpha * n; C.b0 = sig * n * dx * sf; C.r = &r; C.tabs = P.tabs;
+                                    const Real dt = Real(G.st->dt);
+                                    IntResult<Real> R = integrate_cell<Real, 1>(C, dval, dt, sig);
+                                    Real dtau_eff = -R.lnfav;
+                                    if (!(dtau_eff >= Real(0))) dtau_eff = Real(0);
+                                    Nout = ColT<Real>::add(Nin, dtau_eff / sig);
+                                    wout = Real(1) / m_max(dtau_eff, tau0);
+                                    sW[h] = wout;
+                                    if (dt > Real(0)) {
+                                        G.xout[g] = R.x;
+                                        const double nV = double(n) * G.st->cell_volume;
+                                        bud_ions += nV * double(dval - R.x);
+                                        bud_rec += nV * double(R.IR);
+                                        bud_grid = J.grid;
+                                    }
                                 }
                             }
-                            if (ws > Real(0)) sum = ColT<Real>::addc(sum, ColT<Real>::div(acc, ws));
+                            sN[h] = Nout;
                         }
-                        Nin = ColT<Real>::div(sum, Real(ntied));
-                    }
-                    const Real nin_r = ColT<Real>::to_real(Nin);
-                    sI[e] = nin_r;
-                    if (MODE == 0) {
-                        sN[hidx(li, lj, lk)] = ColT<Real>::add(Nin, sD[e]);
-                    } else {
-                        // A1 (Eq. 3): integrate the cell with its entry column
-                        // frozen; pass on N_in - ln<f>/sigma0
-                        const int X = J.sg[0] > 0 ? J.v[0] + i : J.v[0] - 1 - i;
-                        const int Y = J.sg[1] > 0 ? J.v[1] + j : J.v[1] - 1 - j;
-                        const int Z = J.sg[2] > 0 ? J.v[2] + k : J.v[2] - 1 - k;
-                        const long long g = (long long)X + (long long)G.nx * ((long long)Y + (long long)G.ny * Z);
-                        const Real n = G.n ? __ldg(G.n + g) : G.n_uniform;
-                        const Real c0 = Real(i) + Real(0.5), c1 = Real(j) + Real(0.5), c2r = Real(k) + Real(0.5);
-                        const Real r2 = c0 * c0 + c1 * c1 + c2r * c2r;
-                        const Real cmr = m_max(c0, m_max(c1, c2r));
-                        const Real sf = m_sqrt(r2) / cmr;
-                        SrcRate<Real> r;
-                        const int s = J.src;
-                        r.Nin = nin_r;
-                        r.tab = G.tab[s];
-                        if (r.tab < 0) {
-                            r.A = G.qfac[s] * m_exp(-sig * nin_r) / (n * r2 * sf);
-                            r.b = sig * n * dx * sf;
-                            r.p = Real(1);
-                        } else {
-                            r.A = G.qfac[s] / (n * r2 * sf);
-                            r.b = n * dx * sf;
-                            r.p = m_exp(tab_lnp(P.tabs[r.tab], nin_r));
+                        // downstream faces are published as their cells complete
+                        if (li == TX - 1) {
+                            st_face<Col>(faceN + fbase + 0 * FMAX + lk * TY + lj, Nout);
+                            __stcg(P.faceW + fbase + 0 * FMAX + lk * TY + lj, wout);
                         }
-                        CellODE<Real> C;
-                        C.ns = 1; C.c = G.alpha * n; C.b0 = sig * n * dx * sf; C.r = &r; C.tabs = P.tabs;
-                        const Real dt = Real(G.st->dt);
-                        IntResult<Real> R = integrate_cell<Real, 1>(C, sD[e], dt, sig);
-                        Real dtau_eff = -R.lnfav;
-                        if (!(dtau_eff >= Real(0))) dtau_eff = Real(0);
-                        sN[hidx(li, lj, lk)] = ColT<Real>::add(Nin, dtau_eff / sig);
-                        sW[hidx(li, lj, lk)] = Real(1) / m_max(dtau_eff, tau0);
-                        if (dt > Real(0)) {
-                            G.xout[g] = R.x;
-                            const double nV = double(n) * G.st->cell_volume;
-                            bud_ions += nV * double(sD[e] - R.x);
-                            bud_rec += nV * double(R.IR);
-                            bud_grid = J.grid;
+                        if (lj == TY - 1) {
+                            st_face<Col>(faceN + fbase + 1 * FMAX + lk * TX + li, Nout);
+                            __stcg(P.faceW + fbase + 1 * FMAX + lk * TX + li, wout);
+                        }
+                        if (lk == TZ - 1) {
+                            st_face<Col>(faceN + fbase + 2 * FMAX + lj * TX + li, Nout);
+                            __stcg(P.faceW + fbase + 2 * FMAX + lj * TX + li, wout);
                         }
                     }
+                    chain_sync<NT>();
                 }
+                // 3. progress: planes < m1 are done and their face cells written
+                if (tid == 0 && tile_self != P.skip_publish) st_release(P.flags + tile_self, (unsigned)m1);
             }
-            __syncthreads();
-        }
 
-        // 5. publish the downstream faces, then write the entry columns
-        {
-            const long long base = tile_self * 3 * FMAX;
-            for (int q = tid; q < TY * TZ; q += NT) {
-                const int lj = q % TY, lk = q / TY;
-                const int h = hidx(TX - 1, lj, lk);
-                faceN[base + 0 * FMAX + q] = sN[h];
-                P.faceW[base + 0 * FMAX + q] = sW[h];
-            }
-            for (int q = tid; q < TX * TZ; q += NT) {
-                const int li = q % TX, lk = q / TX;
-                const int h = hidx(li, TY - 1, lk);
-                faceN[base + 1 * FMAX + q] = sN[h];
-                P.faceW[base + 1 * FMAX + q] = sW[h];
-            }
-            for (int q = tid; q < TX * TY; q += NT) {
-                const int li = q % TX, lj = q / TX;
-                const int h = hidx(li, lj, TZ - 1);
-                faceN[base + 2 * FMAX + q] = sN[h];
-                P.faceW[base + 2 * FMAX + q] = sW[h];
-            }
-        }
-        __syncthreads();
-        if (tid == 0 && tile_self != P.skip_publish) {
-            __threadfence();
-            st_release(P.flags + tile_self, 1u);
-        }
-        {
+            // 4. entry columns of the tile's cells
             Real *Nout = (P.which == 1 ? G.N2 : G.N1) + (long long)J.src * G.ncell;
             for (int e = tid; e < NC; e += NT) {
                 const int li = e % TX, lj = (e / TX) % TY, lk = e / (TX * TY);
@@ -344,7 +564,7 @@ sweep_kernel(SweepParams<Real> P)
                     const int Y = J.sg[1] > 0 ? J.v[1] + j : J.v[1] - 1 - j;
                     const int Z = J.sg[2] > 0 ? J.v[2] + k : J.v[2] - 1 - k;
                     const long long g = (long long)X + (long long)G.nx * ((long long)Y + (long long)G.ny * Z);
-                    Nout[g] = sI[e];
+                    Nout[g] = sDI[L::h(li, lj, lk)];
                 }
             }
         }
@@ -375,15 +595,14 @@ sweep_kernel(SweepParams<Real> P)
 template <typename Real, int TX, int TY, int TZ>
 constexpr size_t sweep_smem()
 {
-    return (size_t)(TX + 1) * (TY + 1) * (TZ + 1) * (sizeof(typename ColT<Real>::type) + sizeof(Real))
-         + (size_t)4 * TX * TY * TZ * sizeof(Real) + (size_t)TX * TY * TZ;
+    return (size_t)TileLayout<TX, TY, TZ>::HSZ * (sizeof(typename ColT<Real>::type) + 5 * sizeof(Real) + 1);
 }
 
 template <typename Real, int TX, int TY, int TZ, int MODE>
 static cudaError_t launch_shape(const SweepParams<Real> &P, int nblocks, cudaStream_t s)
 {
     constexpr size_t sm = sweep_smem<Real, TX, TY, TZ>();
-    sweep_kernel<Real, TX, TY, TZ, MODE><<<nblocks, TY * TZ, sm, s>>>(P);
+    sweep_kernel<Real, TX, TY, TZ, MODE><<<nblocks, TY * TZ + 32, sm, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -424,8 +643,8 @@ int sweep_occupancy(int shape, int mode)
 #define OOTS_OCC(ID, TX, TY, TZ)                                                                      \
     if (shape == ID) {                                                                                \
         constexpr size_t sm = sweep_smem<Real, TX, TY, TZ>();                                         \
-        if (mode == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 0>, TY * TZ, sm); \
-        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 1>, TY * TZ, sm); \
+        if (mode == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 0>, TY * TZ + 32, sm); \
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 1>, TY * TZ + 32, sm); \
     }
     OOTS_SHAPES(OOTS_OCC)
 #undef OOTS_OCC
