@@ -226,11 +226,15 @@ def run_ours(args, rank, world, local_rank):
         for k, ms in cm.profile_substep():
             prof.setdefault(k, []).append(ms)
     prof_avg = {k: sum(v) / len(v) for k, v in prof.items()}
-    dom = max((k for k in prof_avg if k.startswith(("sweep", "half", "full", "ratedt"))), key=lambda k: prof_avg[k])
+    launches_per_substep = sum(len(v) for v in prof.values()) // 3
+    # an integration is its closed-form pass plus its general pass over the queued cells
+    kern = {k: prof_avg.get(k, 0.0) + prof_avg.get(k + "_general", 0.0) for k in ("half", "full")}
+    kern.update({k: prof_avg[k] for k in ("sweep1", "sweep2", "ratedt") if k in prof_avg})
+    dom = max(kern, key=lambda k: kern[k])
     peak, peak_src = _peaks()
     nsrc = len(w.sources)
     bpc = _bytes_per_cell(dom, 4, nsrc, w.uniform_n is None)
-    achieved = bpc * w.ncell / (prof_avg[dom] / 1e3) / 1e9
+    achieved = bpc * w.ncell / (kern[dom] / 1e3) / 1e9
     step_bytes = sum(_bytes_per_cell(k, 4, nsrc, w.uniform_n is None) for k in ("sweep1", "ratedt", "half", "sweep2", "full"))
 
     # ---------------- plain FP64 beside it ----------------
@@ -284,13 +288,14 @@ def run_ours(args, rank, world, local_rank):
         "fp64": {"value": value_fp64, "ms_per_step": t_fp64 / k64, "steps": k64},
         "mixed_over_fp64": value / value_fp64,
         "accuracy_vs_fp64": acc,
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": dom + (" (closed-form + general pass)" if dom in ("half", "full") else ""),
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
                      "bytes_per_cell": bpc, "step_bytes_per_cell": step_bytes,
                      "step_frac": step_bytes * w.ncell / (t_mixed / args.steps / 1e3) / 1e9 / peak},
         "kernel_ms": prof_avg,
         "e2e": e2e,
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": launches_per_substep * args.steps,
         "clocks": clk,
     }
     if not args.no_cpu_baseline:

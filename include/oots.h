@@ -180,6 +180,8 @@ int oots_run_substeps(oots_ctx *ctx, long long n, double t_end);
 #define OOTS_K_FULL      6   /* full-step integration and photon budget  */
 #define OOTS_K_FINAL1    7   /* close the substep                        */
 #define OOTS_K_IMPLICIT  8   /* implicit sweep (A1)                      */
+#define OOTS_K_HALF_GENERAL 9  /* half step, cells no closed form settles (one warp each) */
+#define OOTS_K_FULL_GENERAL 10 /* full step, cells no closed form settles (one warp each) */
 int oots_profile_substep(oots_ctx *ctx, int *kinds, double *ms, int nmax, int *n_out);
 
 /* ---- read-back --------------------------------------------------------------------------- */

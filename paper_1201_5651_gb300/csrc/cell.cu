@@ -3,6 +3,14 @@
 // integrations of Eq. 2 with frozen entry columns, and the photon budget.
 // Elementwise over every cell of every grid of the call; one flat index space,
 // grids located by binary search over their cell offsets.
+//
+// The integrations run in two passes.  The first pass settles every cell that
+// a closed form covers (photon-free, at its root, or slow enough for the
+// linearised step: almost all of them) and appends the others to a queue.
+// The second pass gives each queued cell a whole warp: the quadrature nodes
+// of every panel are evaluated one per lane, so the few slow cells near the
+// ionisation front neither hold up warps of fast cells nor run their node
+// evaluations one after another.
 #include "common.cuh"
 #include "integrator.cuh"
 #include "kernels.h"
@@ -64,7 +72,8 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 
 template <typename Real, int OP, int NSMAX>
 __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, int ngrid, const long long *offsets,
-                                                   long long total, const DevTable<Real> *tabs)
+                                                   long long total, const DevTable<Real> *tabs, unsigned *queue,
+                                                   unsigned *qcount)
 {
     __shared__ double sh[32];
     __shared__ int s_grid_lo, s_grid_hi;
@@ -87,6 +96,7 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
         const bool active = mine && (OP == OP_RATEDT || dtd > 0.0) && !(OP == OP_RATEDT && st->done);
         double dtmin = __longlong_as_double(0x7ff0000000000000ll);
         double ions = 0.0, rec = 0.0;
+        bool defer = false;
         if (active) {
             const long long g = idx - offsets[gi];
             const int X = (int)(g % G.nx);
@@ -110,15 +120,34 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
                     if (st->K3 > 0) dtmin = fmin(dtmin, st->K3 * fmax(0.05, (double)x0) / xd);
                     if (st->K4 > 0) dtmin = fmin(dtmin, st->K4 / xd);
                 }
-            } else if (OP == OP_HALF) {
-                IntResult<Real> R = integrate_cell<Real, NSMAX>(C, x0, Real(0.5 * dtd), G.sigma0);
-                const_cast<Real *>(G.xh)[g] = R.x;
             } else {
-                IntResult<Real> R = integrate_cell<Real, NSMAX>(C, x0, Real(dtd), G.sigma0);
-                G.xout[g] = R.x;
-                const double nV = double(n) * st->cell_volume;
-                ions = nV * (double(x0) - double(R.x));
-                rec = nV * double(R.IR);
+                // closed forms here; the rest goes to the warp-per-cell pass
+                IntResult<Real> R;
+                Real F0, dF0, f0;
+                const Real h = Real(OP == OP_HALF ? 0.5 * dtd : dtd);
+                if (integrate_prelude<Real, NSMAX>(C, x0, h, G.sigma0, R, F0, dF0, f0)) {
+                    if (OP == OP_HALF) {
+                        const_cast<Real *>(G.xh)[g] = R.x;
+                    } else {
+                        G.xout[g] = R.x;
+                        const double nV = double(n) * st->cell_volume;
+                        ions = nV * (double(x0) - double(R.x));
+                        rec = nV * double(R.IR);
+                    }
+                } else {
+                    defer = true;
+                }
+            }
+        }
+        if (OP != OP_RATEDT) {
+            // warp-aggregated append to the queue of the general pass
+            const unsigned m = __ballot_sync(0xffffffffu, defer);
+            if (m) {
+                const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+                unsigned base = 0;
+                if (lane == leader) base = atomicAdd(qcount + (OP == OP_HALF ? 0 : 1), (unsigned)__popc(m));
+                base = __shfl_sync(0xffffffffu, base, leader);
+                if (defer) queue[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)idx;
             }
         }
         if (OP == OP_RATEDT) {
@@ -145,12 +174,88 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
     }
 }
 
+// General pass: one warp per queued cell (HALF: queue 0, FULL: queue 1).
+// Every lane forms the same rates and runs the same root search; the
+// quadrature nodes are spread over the lanes (WarpEval).  Budget sums of FULL
+// are gathered per block in shared memory for up to eight grids and flushed
+// with one atomic per grid and block.
+template <typename Real, int OP, int NSMAX>
+__global__ void __launch_bounds__(256) cell_general_kernel(const GridDev<Real> *grids, int ngrid, const long long *offsets,
+                                                           const DevTable<Real> *tabs, const unsigned *queue,
+                                                           const unsigned *qcount)
+{
+    __shared__ double s_ions[8], s_rec[8];
+    __shared__ int s_gid[8];
+    const int lane = threadIdx.x & 31;
+    if (OP != OP_HALF) {
+        if (threadIdx.x < 8) { s_ions[threadIdx.x] = 0.0; s_rec[threadIdx.x] = 0.0; s_gid[threadIdx.x] = -1; }
+        __syncthreads();
+    }
+    const unsigned nq = qcount[OP == OP_HALF ? 0 : 1];
+    const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+    for (unsigned q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += nw) {
+        const long long idx = queue[q];
+        const int gi = find_grid(offsets, ngrid, idx);
+        const GridDev<Real> &G = grids[gi];
+        DevState *st = G.st;
+        const double dtd = st->dt;
+        const long long g = idx - offsets[gi];
+        const int X = (int)(g % G.nx);
+        const int Y = (int)((g / G.nx) % G.ny);
+        const int Z = (int)(g / ((long long)G.nx * G.ny));
+        const Real n = G.n ? G.n[g] : G.n_uniform;
+        const Real x0 = G.x[g];
+        SrcRate<Real> r[NSMAX];
+        const Real *Ncol = (OP == OP_FULL2) ? G.N2 : G.N1;
+        CellODE<Real> C;
+        C.ns = cell_rates<Real, NSMAX>(G, Ncol, tabs, X, Y, Z, g, n, r);
+        C.c = G.alpha * n;
+        C.b0 = Real(0);
+        C.r = r;
+        C.tabs = tabs;
+        const Real h = Real(OP == OP_HALF ? 0.5 * dtd : dtd);
+        IntResult<Real> R;
+        Real F0, dF0, f0;
+        if (!integrate_prelude<Real, NSMAX>(C, x0, h, G.sigma0, R, F0, dF0, f0))
+            R = integrate_general<Real, NSMAX>(C, x0, h, G.sigma0, R, F0, dF0, f0, WarpEval{lane});
+        if (lane == 0) {
+            if (OP == OP_HALF) {
+                const_cast<Real *>(G.xh)[g] = R.x;
+            } else {
+                G.xout[g] = R.x;
+                const double nV = double(n) * st->cell_volume;
+                const double ions = nV * (double(x0) - double(R.x)), rec = nV * double(R.IR);
+                const int slot = gi & 7;
+                const int owner = atomicCAS(&s_gid[slot], -1, gi);
+                if (owner == -1 || owner == gi) {
+                    atomicAdd(&s_ions[slot], ions);
+                    atomicAdd(&s_rec[slot], rec);
+                } else {
+                    atomicAdd(&st->bud_step[1], ions + rec);
+                    atomicAdd(&st->bud_step[2], ions);
+                    atomicAdd(&st->bud_step[3], rec);
+                }
+            }
+        }
+    }
+    if (OP != OP_HALF) {
+        __syncthreads();
+        if (threadIdx.x < 8 && s_gid[threadIdx.x] >= 0) {
+            DevState *st = grids[s_gid[threadIdx.x]].st;
+            atomicAdd(&st->bud_step[1], s_ions[threadIdx.x] + s_rec[threadIdx.x]);
+            atomicAdd(&st->bud_step[2], s_ions[threadIdx.x]);
+            atomicAdd(&st->bud_step[3], s_rec[threadIdx.x]);
+        }
+    }
+}
+
 // stage 0: choose dt (Eq. 4 minimum or fixed, capped at t_end - t) and reset the step budget
 // stage 1: close the substep (t += dt, totals, done flag)
 template <typename Real>
-__global__ void finalize_kernel(const GridDev<Real> *grids, int ngrid, int stage)
+__global__ void finalize_kernel(const GridDev<Real> *grids, int ngrid, int stage, unsigned *qcount)
 {
     const int gi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (stage == 0 && gi == 0) { qcount[0] = 0u; qcount[1] = 0u; }
     if (gi >= ngrid) return;
     DevState *st = grids[gi].st;
     if (stage == 0) {
@@ -179,15 +284,19 @@ __global__ void finalize_kernel(const GridDev<Real> *grids, int ngrid, int stage
 
 template <typename Real, int NSMAX>
 static cudaError_t launch_cell_ns(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
-                                  const DevTable<Real> *tabs, int op, cudaStream_t s)
+                                  const DevTable<Real> *tabs, int op, unsigned *queue, unsigned *qcount,
+                                  int gen_blocks, cudaStream_t s)
 {
     const int bs = 256;
     const long long nb = (total + bs - 1) / bs;
     switch (op) {
-    case OP_RATEDT: cell_kernel<Real, OP_RATEDT, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs); break;
-    case OP_HALF: cell_kernel<Real, OP_HALF, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs); break;
-    case OP_FULL1: cell_kernel<Real, OP_FULL1, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs); break;
-    case OP_FULL2: cell_kernel<Real, OP_FULL2, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs); break;
+    case OP_RATEDT: cell_kernel<Real, OP_RATEDT, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount); break;
+    case OP_HALF: cell_kernel<Real, OP_HALF, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount); break;
+    case OP_FULL1: cell_kernel<Real, OP_FULL1, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount); break;
+    case OP_FULL2: cell_kernel<Real, OP_FULL2, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount); break;
+    case OP_HALF | OP_GENERAL: cell_general_kernel<Real, OP_HALF, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
+    case OP_FULL1 | OP_GENERAL: cell_general_kernel<Real, OP_FULL1, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
+    case OP_FULL2 | OP_GENERAL: cell_general_kernel<Real, OP_FULL2, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -197,25 +306,39 @@ static cudaError_t launch_cell_ns(const GridDev<Real> *grids, int ngrid, const l
 // single-source kernels, whose per-source state stays in registers)
 template <typename Real>
 cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
-                        const DevTable<Real> *tabs, int op, int nsmax, cudaStream_t s)
+                        const DevTable<Real> *tabs, int op, int nsmax, unsigned *queue, unsigned *qcount,
+                        int gen_blocks, cudaStream_t s)
 {
     if (total <= 0) return cudaSuccess;
-    if (nsmax <= 1) return launch_cell_ns<Real, 1>(grids, ngrid, offsets, total, tabs, op, s);
-    return launch_cell_ns<Real, MAX_SRC>(grids, ngrid, offsets, total, tabs, op, s);
+    if (nsmax <= 1) return launch_cell_ns<Real, 1>(grids, ngrid, offsets, total, tabs, op, queue, qcount, gen_blocks, s);
+    return launch_cell_ns<Real, MAX_SRC>(grids, ngrid, offsets, total, tabs, op, queue, qcount, gen_blocks, s);
+}
+
+// Resident 256-thread blocks of the general pass per SM.
+template <typename Real>
+int cell_general_occupancy(int nsmax)
+{
+    int nb = 0;
+    cudaError_t e = nsmax <= 1
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_general_kernel<Real, OP_FULL2, 1>, 256, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_general_kernel<Real, OP_FULL2, MAX_SRC>, 256, 0);
+    return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 
 template <typename Real>
-cudaError_t launch_finalize(const GridDev<Real> *grids, int ngrid, int stage, cudaStream_t s)
+cudaError_t launch_finalize(const GridDev<Real> *grids, int ngrid, int stage, unsigned *qcount, cudaStream_t s)
 {
-    finalize_kernel<Real><<<(ngrid + 63) / 64, 64, 0, s>>>(grids, ngrid, stage);
+    finalize_kernel<Real><<<(ngrid + 63) / 64, 64, 0, s>>>(grids, ngrid, stage, qcount);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_cell<double>(const GridDev<double> *, int, const long long *, long long,
-                                         const DevTable<double> *, int, int, cudaStream_t);
+                                         const DevTable<double> *, int, int, unsigned *, unsigned *, int, cudaStream_t);
 template cudaError_t launch_cell<float>(const GridDev<float> *, int, const long long *, long long,
-                                        const DevTable<float> *, int, int, cudaStream_t);
-template cudaError_t launch_finalize<double>(const GridDev<double> *, int, int, cudaStream_t);
-template cudaError_t launch_finalize<float>(const GridDev<float> *, int, int, cudaStream_t);
+                                        const DevTable<float> *, int, int, unsigned *, unsigned *, int, cudaStream_t);
+template int cell_general_occupancy<double>(int);
+template int cell_general_occupancy<float>(int);
+template cudaError_t launch_finalize<double>(const GridDev<double> *, int, int, unsigned *, cudaStream_t);
+template cudaError_t launch_finalize<float>(const GridDev<float> *, int, int, unsigned *, cudaStream_t);
 
 } // namespace oots

@@ -200,17 +200,50 @@ template <typename Real, int NSMAX>
 OOTS_HD Real attenuation_average(const CellODE<Real> &C, const SrcEq<Real> *Q, Real xe, Real d0, Real Dinf,
                                  Real h, Real ustar, Real ut, bool in_panels, Real wt);
 
-// Integrate one cell from x0 over h.  sigma0 scales the tabulated b (= n ds)
-// to an optical depth for the curvature scale.
+// Node evaluators of the general path: eval<N>(node, invD, dv) fills invD[l]
+// = 1/D and dv[l] = d at the N quadrature nodes l = 0..N-1, where node(l, d)
+// returns 1/D at node l and sets its deviation d.  The sequential form loops;
+// the warp form gives node l to lane l and broadcasts the values, so a whole
+// warp integrates one cell and a panel costs one evaluation of latency.
+struct SeqEval {
+    template <int N, typename Real, typename Node>
+    OOTS_HD __forceinline__ void eval(const Node &node, Real *invD, Real *dv) const
+    {
+#pragma unroll
+        for (int l = 0; l < N; l++) invD[l] = node(l, dv[l]);
+    }
+};
+#ifdef __CUDACC__
+struct WarpEval {
+    int lane;
+    template <int N, typename Real, typename Node>
+    __device__ __forceinline__ void eval(const Node &node, Real *invD, Real *dv) const
+    {
+        static_assert(N <= 32, "one node per lane");
+        Real mi = Real(0), md = Real(0);
+        if (lane < N) mi = node(lane, md);
+#pragma unroll
+        for (int l = 0; l < N; l++) {
+            invD[l] = __shfl_sync(0xffffffffu, mi, l);
+            dv[l] = __shfl_sync(0xffffffffu, md, l);
+        }
+    }
+};
+#endif
+
+// First part of the integration: the closed forms.  Returns true when the
+// cell is done (photon-free, at its root, or slow enough for the linearised
+// step); otherwise F(x0), F'(x0) and f(x0) are left for the general part.
 template <typename Real, int NSMAX = MAX_SRC>
-OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, Real sigma0)
+OOTS_HD bool integrate_prelude(const CellODE<Real> &C, Real x0, Real h, Real sigma0, IntResult<Real> &R,
+                               Real &F0, Real &dF0, Real &f0)
 {
     constexpr int G = IntCfg<Real>::G;
-    IntResult<Real> R;
     R.x = x0;
     R.IR = Real(0);
     R.lnfav = -C.b0 * x0;
-    if (!(h > Real(0))) return R;
+    F0 = dF0 = f0 = Real(0);
+    if (!(h > Real(0))) return true;
 
     // photon-free cell: du/dt = -c u^2, u = 1 - x (closed form)
     bool lit = false;
@@ -232,15 +265,14 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
             }
             R.lnfav = -C.b0 * x0 + m_log(acc);
         }
-        return R;
+        return true;
     }
 
-    Real F0, dF0;
     ode_F<Real, NSMAX>(C, x0, &F0, &dF0);
-    Real f0 = -F0 + C.c * (Real(1) - x0) * (Real(1) - x0);
+    f0 = -F0 + C.c * (Real(1) - x0) * (Real(1) - x0);
     if (f0 == Real(0)) {
         R.IR = h * C.c * (Real(1) - x0) * (Real(1) - x0);
-        return R;
+        return true;
     }
     // slow cells: when h |f'| is small and the step moves x by much less than
     // the scales on which f bends (1/b of every source, and 1 - x for the
@@ -263,27 +295,41 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
                 R.x = x0 + dx;
                 const Real xm = x0 + Real(0.5) * dx;
                 R.IR = h * C.c * (Real(1) - xm) * (Real(1) - xm);
-                return R;
+                return true;
             }
         }
     }
+    return false;
+}
+
+// Second part: the root, then the time-to-state quadrature (see the header).
+// R carries the prelude's defaults; ev evaluates the quadrature nodes.
+#pragma nv_exec_check_disable
+template <typename Real, int NSMAX, typename Eval>
+OOTS_HD IntResult<Real> integrate_general(const CellODE<Real> &C, Real x0, Real h, Real sigma0, IntResult<Real> R,
+                                          Real F0, Real dF0, Real f0, const Eval &ev)
+{
+    constexpr int G = IntCfg<Real>::G;
     // root of the convex, decreasing right-hand side by Newton from x0: from
     // the right of the root the first step lands left of it, and from the left
-    // Newton increases monotonically to it; [lo, hi] brackets the root
+    // Newton increases monotonically to it; [lo, hi] brackets the root.  f is
+    // a difference of two terms, so it is known only to about eps times their
+    // size: Newton also stops once |f| is inside that rounding band (the
+    // iterate would otherwise jitter inside it without meeting the step test).
     Real xe;
     {
         Real lo = f0 > Real(0) ? x0 : Real(0), hi = f0 > Real(0) ? Real(1) : x0;
-        Real xk = x0, fk = f0, dfk = -dF0 - Real(2) * C.c * (Real(1) - x0);
+        Real xk = x0, fk = f0, Fk = F0, dfk = -dF0 - Real(2) * C.c * (Real(1) - x0);
         xe = x0;
-        for (int it = 0; it < 100; it++) {
-            if (fk == Real(0)) { xe = xk; break; }
+        for (int it = 0; it < 60; it++) {
+            if (m_abs(fk) <= Real(32) * RealLimits<Real>::eps() * (m_abs(Fk) + C.c * (Real(1) - xk) * (Real(1) - xk))) break;
             if (fk > Real(0)) lo = m_max(lo, xk); else hi = m_min(hi, xk);
             Real xn = (dfk < Real(0)) ? xk - fk / dfk : Real(0.5) * (lo + hi);
             if (!(xn >= lo && xn <= hi)) xn = Real(0.5) * (lo + hi);
             const bool done = m_abs(xn - xk) <= Real(4) * RealLimits<Real>::eps() * m_max(xn, RealLimits<Real>::tiny())
                            || (hi - lo) <= Real(4) * RealLimits<Real>::eps() * m_max(hi, RealLimits<Real>::tiny());
             xk = xn;
-            Real Fk, dFk;
+            Real dFk;
             ode_F<Real, NSMAX>(C, xk, &Fk, &dFk);
             fk = -Fk + C.c * (Real(1) - xk) * (Real(1) - xk);
             dfk = -dFk - Real(2) * C.c * (Real(1) - xk);
@@ -364,18 +410,29 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
         Real ua = uk - du;
         if (ua < ut) ua = ut;
         Real um = Real(0.5) * (uk + ua);
-        // nodal values of 1/D and c(1-x)^2/D on both halves
+        // nodal values of 1/D on both halves (nodes 0..G-1: upper half [um, uk];
+        // G..2G-1: lower half [ua, um]) and on the whole panel (2G..3G-1)
+        Real iv[3 * G], dvv[3 * G];
+        {
+            const Real ukc = uk, uac = ua, umc = um;
+            auto node = [&](int l, Real &d) {
+                const int part = l / G, g = l - part * G;
+                const Real lo = part == 0 ? umc : uac, hi = part == 1 ? umc : ukc;
+                const Real u = Real(0.5) * (hi + lo) + Real(0.5) * (hi - lo) * GL<G>::template x<Real>(g);
+                d = d0 * m_exp(u);
+                return Real(1) / ode_D<Real, NSMAX>(C, Q, xe, d);
+            };
+            ev.template eval<3 * G>(node, iv, dvv);
+        }
         Real vD[2][G], vR[2][G], Ih[2];
         for (int hh = 0; hh < 2; hh++) {
             const Real lo = hh ? ua : um, hi = hh ? um : uk;     // hh = 0: upper half [um, uk]
-            const Real hw = Real(0.5) * (hi - lo), mid = Real(0.5) * (hi + lo);
+            const Real hw = Real(0.5) * (hi - lo);
             Ih[hh] = Real(0);
 #pragma unroll
             for (int g = 0; g < G; g++) {
-                Real u = mid + hw * GL<G>::template x<Real>(g);
-                Real d = d0 * m_exp(u);
-                Real xi = xe + d;
-                Real invD = Real(1) / ode_D<Real, NSMAX>(C, Q, xe, d);
+                const Real invD = iv[hh * G + g];
+                const Real xi = xe + dvv[hh * G + g];
                 vD[hh][g] = invD;
                 vR[hh][g] = C.c * (Real(1) - xi) * (Real(1) - xi) * invD;
                 Ih[hh] += GL<G>::template w<Real>(g) * hw * invD;
@@ -384,14 +441,9 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
         // the whole panel by one Gauss sum, to estimate the error of the halves
         Real Ifull = Real(0);
         {
-            const Real hw = Real(0.5) * (uk - ua), mid = um;
+            const Real hw = Real(0.5) * (uk - ua);
 #pragma unroll
-            for (int g = 0; g < G; g++) {
-                Real u = mid + hw * GL<G>::template x<Real>(g);
-                Real d = d0 * m_exp(u);
-                Real invD = Real(1) / ode_D<Real, NSMAX>(C, Q, xe, d);
-                Ifull += GL<G>::template w<Real>(g) * hw * invD;
-            }
+            for (int g = 0; g < G; g++) Ifull += GL<G>::template w<Real>(g) * hw * iv[2 * G + g];
         }
         npan++;
         const Real err = m_abs(Ifull - (Ih[0] + Ih[1]));
@@ -446,12 +498,19 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
         Real cR0 = C.c * (Real(1) - xe) * (Real(1) - xe);
         Real qD[G], qR[G];
         const bool smooth = !clamped;
+        Real iv[G], dvv[G];
+        {
+            auto node = [&](int l, Real &d) {
+                d = d0 * (Real(0.5) * wte * (Real(1) + GL<G>::template x<Real>(l)));
+                return Real(1) / ode_D<Real, NSMAX>(C, Q, xe, d);
+            };
+            ev.template eval<G>(node, iv, dvv);
+        }
 #pragma unroll
         for (int g = 0; g < G; g++) {
             Real w = Real(0.5) * wte * (Real(1) + GL<G>::template x<Real>(g));
-            Real d = d0 * w;
-            Real xi = xe + d;
-            Real invD = Real(1) / ode_D<Real, NSMAX>(C, Q, xe, d);
+            Real xi = xe + dvv[g];
+            Real invD = iv[g];
             qD[g] = smooth ? (invD - Real(1) / Dinf) / w : Real(0);
             qR[g] = smooth ? (C.c * (Real(1) - xi) * (Real(1) - xi) * invD - cR0 / Dinf) / w : Real(0);
         }
@@ -491,6 +550,18 @@ OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, 
     R.IR = IR;
     if (C.b0 > Real(0)) R.lnfav = attenuation_average<Real, NSMAX>(C, Q, xe, d0, Dinf, h, ustar, ut, found, wt);
     return R;
+}
+
+
+// Integrate one cell from x0 over h.  sigma0 scales the tabulated b (= n ds)
+// to an optical depth for the curvature scale.
+template <typename Real, int NSMAX = MAX_SRC>
+OOTS_HD IntResult<Real> integrate_cell(const CellODE<Real> &C, Real x0, Real h, Real sigma0)
+{
+    IntResult<Real> R;
+    Real F0, dF0, f0;
+    if (integrate_prelude<Real, NSMAX>(C, x0, h, sigma0, R, F0, dF0, f0)) return R;
+    return integrate_general<Real, NSMAX>(C, x0, h, sigma0, R, F0, dF0, f0, SeqEval());
 }
 
 // Second pass for A1 (Eq. 3): <exp(-b0 x)> over the step, once the end point

@@ -44,12 +44,16 @@ template <typename Real> bool sweep_shape_ok(int shape);              // fits th
 template <typename Real>
 cudaError_t launch_sweep(const SweepParams<Real> &P, int shape, int mode, int nblocks, cudaStream_t s);
 
-// Per-cell passes
-enum { OP_RATEDT = 0, OP_HALF = 1, OP_FULL1 = 2, OP_FULL2 = 3 };
+// Per-cell passes.  HALF and FULL run as a closed-form pass over all cells
+// followed by the general pass (op | OP_GENERAL) over the queued cells.
+enum { OP_RATEDT = 0, OP_HALF = 1, OP_FULL1 = 2, OP_FULL2 = 3, OP_GENERAL = 16 };
 template <typename Real>
 cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
-                        const DevTable<Real> *tabs, int op, int nsmax, cudaStream_t s);
+                        const DevTable<Real> *tabs, int op, int nsmax, unsigned *queue, unsigned *qcount,
+                        int gen_blocks, cudaStream_t s);
+template <typename Real> int cell_general_occupancy(int nsmax);
+// stage 0 also clears the two queue counters
 template <typename Real>
-cudaError_t launch_finalize(const GridDev<Real> *grids, int ngrid, int stage, cudaStream_t s);
+cudaError_t launch_finalize(const GridDev<Real> *grids, int ngrid, int stage, unsigned *qcount, cudaStream_t s);
 
 } // namespace oots

@@ -137,6 +137,9 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     std::vector<void *> tabmem;
     long long *d_offsets = nullptr;
     long long total = 0;
+    unsigned *d_queue = nullptr;       // cells left to the general pass (one entry per cell at most)
+    unsigned *d_qcount = nullptr;      // queue lengths of the half and full integrations
+    int gen_blocks = 1;                // grid of the general pass
     int nblocks0 = 1, nblocks1 = 1;
     int nsmax = 1;                     // largest source count among the grids
     cudaGraph_t graph = nullptr;
@@ -159,6 +162,8 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         cudaFree(d_tabs);
         for (void *p : tabmem) cudaFree(p);
         cudaFree(d_offsets);
+        cudaFree(d_queue);
+        cudaFree(d_qcount);
     }
 
     int upload_table(const HostTable &H, DevTable<Real> &T)
@@ -292,6 +297,10 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         CU(cudaMemcpy(d_grids, grids.data(), grids.size() * sizeof(GridDev<Real>), cudaMemcpyHostToDevice));
         CU(cudaMalloc(&d_offsets, offs.size() * sizeof(long long)));
         CU(cudaMemcpy(d_offsets, offs.data(), offs.size() * sizeof(long long), cudaMemcpyHostToDevice));
+        if (total > 0xffffffffll) return fail(OOTS_E_INVAL, "%lld cells in one call (the queue holds 32-bit indices)", total);
+        CU(cudaMalloc(&d_queue, (size_t)std::max(total, 1ll) * sizeof(unsigned)));
+        CU(cudaMalloc(&d_qcount, 8 * sizeof(unsigned)));
+        CU(cudaMemset(d_qcount, 0, 8 * sizeof(unsigned)));
         if (!jobs.empty()) {
             CU(cudaMalloc(&d_jobs, jobs.size() * sizeof(Job)));
             CU(cudaMemcpy(d_jobs, jobs.data(), jobs.size() * sizeof(Job), cudaMemcpyHostToDevice));
@@ -311,6 +320,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         int nsm = c0->nsm;
         nblocks0 = sweep_occupancy<Real>(shape, 0) * nsm;
         nblocks1 = sweep_occupancy<Real>(shape, 1) * nsm;
+        gen_blocks = cell_general_occupancy<Real>(nsmax) * nsm;
         return OOTS_OK;
     }
 
@@ -347,15 +357,21 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     int cell(cudaStream_t s, int op)
     {
         if (prof) prof->mark(0);
-        CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op, nsmax, s));
+        CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op, nsmax, d_queue, d_qcount, gen_blocks, s));
         if (prof) prof->mark(op == OP_RATEDT ? OOTS_K_RATEDT : (op == OP_HALF ? OOTS_K_HALF : OOTS_K_FULL));
+        if (op == OP_RATEDT) return OOTS_OK;
+        // the cells no closed form settles, one warp each
+        if (prof) prof->mark(0);
+        CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op | OP_GENERAL, nsmax, d_queue,
+                             d_qcount, gen_blocks, s));
+        if (prof) prof->mark(op == OP_HALF ? OOTS_K_HALF_GENERAL : OOTS_K_FULL_GENERAL);
         return OOTS_OK;
     }
 
     int fin(cudaStream_t s, int stage)
     {
         if (prof) prof->mark(0);
-        CU(launch_finalize<Real>(d_grids, (int)ctxs.size(), stage, s));
+        CU(launch_finalize<Real>(d_grids, (int)ctxs.size(), stage, d_qcount, s));
         if (prof) prof->mark(stage == 0 ? OOTS_K_FINAL0 : OOTS_K_FINAL1);
         return OOTS_OK;
     }

@@ -40,7 +40,8 @@ EXPORTS = [
     "oots_tile_shape_info", "oots_debug_set", "oots_version", "oots_run_substeps", "oots_profile_substep",
     "oots_trace_noalloc",
 ]
-KERNEL_KINDS = {1: "sweep1", 2: "ratedt", 3: "final0", 4: "half", 5: "sweep2", 6: "full", 7: "final1", 8: "implicit"}
+KERNEL_KINDS = {1: "sweep1", 2: "ratedt", 3: "final0", 4: "half", 5: "sweep2", 6: "full", 7: "final1", 8: "implicit",
+                9: "half_general", 10: "full_general"}
 
 
 class OotsError(RuntimeError):
