@@ -170,10 +170,16 @@ def run_ours(args, rank, world, local_rank):
         s = torch.cuda.Stream(device=dev)
         c.set_stream(s.cuda_stream)
         c.advance(args.t0 * w.t_rec)          # untimed: develop the front
+        shape = None
         if args.shape >= 0:
-            c.set_tile_shape(args.shape)
-        else:
-            tuned[precision] = autotune.tune(c, devname, len(w.sources), use_cache=not args.retune)
+            try:
+                c.set_tile_shape(args.shape)
+                c.profile_substep()           # builds the launch set: refuses a shape that does not fit
+                shape = args.shape
+            except oots.OotsError:
+                shape = None                  # not at this precision: tune instead
+        tuned[precision] = shape if shape is not None else autotune.tune(c, devname, len(w.sources),
+                                                                          use_cache=not args.retune)
         return c, s
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=f"cuda:{dev}")   # 256 MB > L2

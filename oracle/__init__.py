@@ -79,6 +79,8 @@ def _load():
         lib.or_substep.argtypes = [P, ctypes.POINTER(_Scheme), dp, dp, ctypes.c_double, dp, dp]
         lib.or_substep.restype = ctypes.c_double
         lib.or_long_char.argtypes = [P, ctypes.c_int, dp, dp]
+        lib.or_integrate_cells.argtypes = [P, ctypes.c_long, ctypes.c_void_p, dp, dp, ctypes.c_double, dp]
+        lib.or_integrate_cells.restype = None
         lib.or_long_char.restype = None
         lib.or_compute_dt.argtypes = [P, ctypes.POINTER(_Scheme), dp]
         lib.or_compute_dt.restype = ctypes.c_double
@@ -175,6 +177,17 @@ class Problem:
         F = np.zeros_like(x); xd = np.zeros_like(x)
         _load().or_rates(ctypes.byref(self.st), _ptr(x), _ptr(Nin), _ptr(F), _ptr(xd))
         return F, xd
+
+    def integrate_cells(self, idx: np.ndarray, x0: np.ndarray, Nin: np.ndarray, h: float) -> np.ndarray:
+        """x(h) of the cells with flat indices idx from x0, entry columns Nin (nsrc, nz, ny, nx) frozen."""
+        idx = np.ascontiguousarray(idx, np.int64)
+        x0 = np.ascontiguousarray(x0, np.float64)
+        Nin = np.ascontiguousarray(Nin, np.float64)
+        assert Nin.size == max(self.nsrc, 1) * self.ncell and x0.size == idx.size
+        out = np.zeros(idx.size)
+        _load().or_integrate_cells(ctypes.byref(self.st), idx.size, idx.ctypes.data, _ptr(x0), _ptr(Nin), float(h),
+                                   _ptr(out))
+        return out
 
     def lnp(self, s: int, N: float) -> float:
         return _load().or_lnp(ctypes.byref(self.st), s, N)

@@ -846,6 +846,26 @@ static void integrate_all(const or_problem *p, const double *x0, const double *N
 }
 
 /*
+ * Selected cells of integrate_all (Sect. 2.2: Eq. 2 over h from x0 with the
+ * entry columns Nin[s*ncell + gi] frozen), for checks on grids too large to
+ * integrate whole: cell idx[q] starts from x0[q]; xout[q] = x(h).
+ */
+void or_integrate_cells(const or_problem *p, long nq, const long *idx, const double *x0, const double *Nin,
+                        double h, double *xout)
+{
+    long ncell = (long)p->nx * p->ny * p->nz;
+    or_srcrate *r = (or_srcrate *)malloc(sizeof(or_srcrate) * (p->nsrc > 0 ? p->nsrc : 1));
+    for (long q = 0; q < nq; q++) {
+        long gi = idx[q];
+        int X = (int)(gi % p->nx), Y = (int)((gi / p->nx) % p->ny), Z = (int)(gi / ((long)p->nx * p->ny));
+        cell_rates(p, X, Y, Z, gi, ncell, Nin, r);
+        or_cell C = {p->nsrc, r, p->alpha * p->nH[gi], 0.0};
+        xout[q] = or_integrate_cell(&C, x0[q], h).x;
+    }
+    free(r);
+}
+
+/*
  * A1 (Sect. 2.1): one sweep per octant in which every cell, in causal order,
  * takes its entry column from the time-averaged columns of its upwind
  * neighbours, integrates (x, attenuation) over dt, and hands downstream the

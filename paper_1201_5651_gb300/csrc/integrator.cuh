@@ -200,12 +200,51 @@ template <typename Real, int NSMAX>
 OOTS_HD Real attenuation_average(const CellODE<Real> &C, const SrcEq<Real> *Q, Real xe, Real d0, Real Dinf,
                                  Real h, Real ustar, Real ut, bool in_panels, Real wt);
 
-// Node evaluators of the general path: eval<N>(node, invD, dv) fills invD[l]
-// = 1/D and dv[l] = d at the N quadrature nodes l = 0..N-1, where node(l, d)
-// returns 1/D at node l and sets its deviation d.  The sequential form loops;
-// the warp form gives node l to lane l and broadcasts the values, so a whole
-// warp integrates one cell and a panel costs one evaluation of latency.
+// Root of the convex, decreasing right-hand side by Newton inside the
+// bracket [lo, hi], from xk (with f, F and f' there): from the right of the
+// root the first step lands left of it, and from the left Newton increases
+// monotonically to it.  f is a difference of two terms, so it is known only to
+// about eps times their size: Newton also stops once |f| is inside that
+// rounding band (the iterate would otherwise jitter inside it without meeting
+// the step test).
+template <typename Real, int NSMAX>
+OOTS_HD Real newton_root(const CellODE<Real> &C, Real lo, Real hi, Real xk, Real fk, Real Fk, Real dfk)
+{
+    Real xe = xk;
+    for (int it = 0; it < 60; it++) {
+        if (m_abs(fk) <= Real(32) * RealLimits<Real>::eps() * (m_abs(Fk) + C.c * (Real(1) - xk) * (Real(1) - xk))) break;
+        if (fk > Real(0)) lo = m_max(lo, xk); else hi = m_min(hi, xk);
+        Real xn = (dfk < Real(0)) ? xk - fk / dfk : Real(0.5) * (lo + hi);
+        if (!(xn >= lo && xn <= hi)) xn = Real(0.5) * (lo + hi);
+        const bool done = m_abs(xn - xk) <= Real(4) * RealLimits<Real>::eps() * m_max(xn, RealLimits<Real>::tiny())
+                       || (hi - lo) <= Real(4) * RealLimits<Real>::eps() * m_max(hi, RealLimits<Real>::tiny());
+        xk = xn;
+        Real dFk;
+        ode_F<Real, NSMAX>(C, xk, &Fk, &dFk);
+        fk = -Fk + C.c * (Real(1) - xk) * (Real(1) - xk);
+        dfk = -dFk - Real(2) * C.c * (Real(1) - xk);
+        xe = xk;
+        if (done) break;
+    }
+    return xe;
+}
+
+// Evaluators of the general path.
+//  - root(C, x0, f0, F0, dF0): the root x_eq of f.
+//  - eval<N>(node, invD, dv): fills invD[l] = 1/D and dv[l] = d at the N
+//    quadrature nodes l = 0..N-1, where node(l, d) returns 1/D at node l and
+//    sets its deviation d.
+// The sequential form runs Newton from x0 and loops over the nodes.  The warp
+// form brackets the root with 32 samples at once and gives node l to lane l,
+// broadcasting the values: a whole warp integrates one cell, a panel costs one
+// evaluation of latency and the root search a scan plus a short polish.
 struct SeqEval {
+    template <typename Real, int NSMAX>
+    OOTS_HD Real root(const CellODE<Real> &C, Real x0, Real f0, Real F0, Real dF0) const
+    {
+        const Real lo = f0 > Real(0) ? x0 : Real(0), hi = f0 > Real(0) ? Real(1) : x0;
+        return newton_root<Real, NSMAX>(C, lo, hi, x0, f0, F0, -dF0 - Real(2) * C.c * (Real(1) - x0));
+    }
     template <int N, typename Real, typename Node>
     OOTS_HD __forceinline__ void eval(const Node &node, Real *invD, Real *dv) const
     {
@@ -216,6 +255,37 @@ struct SeqEval {
 #ifdef __CUDACC__
 struct WarpEval {
     int lane;
+    // Lane l samples f at a point of the bracket, ascending in x with l and
+    // geometric towards the end the root lies away from (x for a root below
+    // x0, 1 - x for a root above it) over nine decades; f > 0 exactly left
+    // of the root, so the ballot of f > 0 marks the lanes below it.  Newton
+    // polishes from the left end of the sign change.
+    template <typename Real, int NSMAX>
+    __device__ Real root(const CellODE<Real> &C, Real x0, Real f0, Real F0, Real dF0) const
+    {
+        const bool above = f0 > Real(0);                     // root in (x0, 1]
+        const Real span = above ? Real(1) - x0 : x0;
+        // ratio e^-0.6476 per lane: 32 samples over nine decades of the span
+        const Real p = above ? Real(1) - span * m_exp(Real(-0.6476) * Real(lane + 1))
+                             : span * m_exp(Real(-0.6476) * Real(32 - lane));
+        Real Fp, dFp;
+        ode_F<Real, NSMAX>(C, p, &Fp, &dFp);
+        const Real fp = -Fp + C.c * (Real(1) - p) * (Real(1) - p);
+        const Real dfp = -dFp - Real(2) * C.c * (Real(1) - p);
+        const unsigned pos = __ballot_sync(0xffffffffu, fp > Real(0));
+        const int j = (pos == 0xffffffffu) ? 32 : __ffs(~pos) - 1;   // first sample right of the root
+        // bracket [lo, hi] and the starting end
+        const Real pj = __shfl_sync(0xffffffffu, p, j & 31), pjm = __shfl_sync(0xffffffffu, p, (j + 31) & 31);
+        const Real fjm = __shfl_sync(0xffffffffu, fp, (j + 31) & 31), Fjm = __shfl_sync(0xffffffffu, Fp, (j + 31) & 31);
+        const Real dfjm = __shfl_sync(0xffffffffu, dfp, (j + 31) & 31);
+        const Real fj = __shfl_sync(0xffffffffu, fp, j & 31), Fj = __shfl_sync(0xffffffffu, Fp, j & 31);
+        const Real dfj = __shfl_sync(0xffffffffu, dfp, j & 31);
+        const Real lo = j > 0 ? pjm : (above ? x0 : Real(0));
+        const Real hi = j < 32 ? pj : (above ? Real(1) : x0);
+        if (j > 0) return newton_root<Real, NSMAX>(C, lo, hi, pjm, fjm, Fjm, dfjm);
+        if (above) return newton_root<Real, NSMAX>(C, lo, hi, x0, f0, F0, -dF0 - Real(2) * C.c * (Real(1) - x0));
+        return newton_root<Real, NSMAX>(C, lo, hi, pj, fj, Fj, dfj);
+    }
     template <int N, typename Real, typename Node>
     __device__ __forceinline__ void eval(const Node &node, Real *invD, Real *dv) const
     {
@@ -270,7 +340,8 @@ OOTS_HD bool integrate_prelude(const CellODE<Real> &C, Real x0, Real h, Real sig
 
     ode_F<Real, NSMAX>(C, x0, &F0, &dF0);
     f0 = -F0 + C.c * (Real(1) - x0) * (Real(1) - x0);
-    if (f0 == Real(0)) {
+    // at the root to within the rounding of f: x stays
+    if (m_abs(f0) <= Real(32) * RealLimits<Real>::eps() * (m_abs(F0) + C.c * (Real(1) - x0) * (Real(1) - x0))) {
         R.IR = h * C.c * (Real(1) - x0) * (Real(1) - x0);
         return true;
     }
@@ -310,33 +381,7 @@ OOTS_HD IntResult<Real> integrate_general(const CellODE<Real> &C, Real x0, Real 
                                           Real F0, Real dF0, Real f0, const Eval &ev)
 {
     constexpr int G = IntCfg<Real>::G;
-    // root of the convex, decreasing right-hand side by Newton from x0: from
-    // the right of the root the first step lands left of it, and from the left
-    // Newton increases monotonically to it; [lo, hi] brackets the root.  f is
-    // a difference of two terms, so it is known only to about eps times their
-    // size: Newton also stops once |f| is inside that rounding band (the
-    // iterate would otherwise jitter inside it without meeting the step test).
-    Real xe;
-    {
-        Real lo = f0 > Real(0) ? x0 : Real(0), hi = f0 > Real(0) ? Real(1) : x0;
-        Real xk = x0, fk = f0, Fk = F0, dfk = -dF0 - Real(2) * C.c * (Real(1) - x0);
-        xe = x0;
-        for (int it = 0; it < 60; it++) {
-            if (m_abs(fk) <= Real(32) * RealLimits<Real>::eps() * (m_abs(Fk) + C.c * (Real(1) - xk) * (Real(1) - xk))) break;
-            if (fk > Real(0)) lo = m_max(lo, xk); else hi = m_min(hi, xk);
-            Real xn = (dfk < Real(0)) ? xk - fk / dfk : Real(0.5) * (lo + hi);
-            if (!(xn >= lo && xn <= hi)) xn = Real(0.5) * (lo + hi);
-            const bool done = m_abs(xn - xk) <= Real(4) * RealLimits<Real>::eps() * m_max(xn, RealLimits<Real>::tiny())
-                           || (hi - lo) <= Real(4) * RealLimits<Real>::eps() * m_max(hi, RealLimits<Real>::tiny());
-            xk = xn;
-            Real dFk;
-            ode_F<Real, NSMAX>(C, xk, &Fk, &dFk);
-            fk = -Fk + C.c * (Real(1) - xk) * (Real(1) - xk);
-            dfk = -dFk - Real(2) * C.c * (Real(1) - xk);
-            xe = xk;
-            if (done) break;
-        }
-    }
+    const Real xe = ev.template root<Real, NSMAX>(C, x0, f0, F0, dF0);
     Real d0 = x0 - xe;
     if (d0 == Real(0)) {
         R.IR = h * C.c * (Real(1) - x0) * (Real(1) - x0);

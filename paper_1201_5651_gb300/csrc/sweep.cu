@@ -19,7 +19,10 @@
 // halo cells are covered by transitivity (the face-adjacent upstream tile
 // waited for them before it completed the plane we wait for).
 //
-// Each CTA holds the chain warps and one producer warp.  The producer waits
+// Each CTA holds the chain warps, one producer warp and one publisher warp.
+// The publisher turns the chain's per-chunk completion (a shared-memory
+// counter) into the GPU-scope release of the tile's progress, so the release
+// fence never stalls the chain.  The producer waits
 // (bounded spin, acquire) for the upstream progress each chunk needs and
 // stages that chunk's halo cells (a compile-time list sorted by the first
 // plane that reads them) from the published faces into shared memory, running
@@ -165,7 +168,7 @@ template <int TX, int TY, int TZ>
 __device__ const HaloList<TX, TY, TZ> g_halo_list = make_halo_list<TX, TY, TZ>();
 
 template <typename Real, int TX, int TY, int TZ, int MODE>
-__global__ void __launch_bounds__(TY *TZ + 32)
+__global__ void __launch_bounds__(TY *TZ + 64)
 sweep_kernel(SweepParams<Real> P)
 {
     typedef typename ColT<Real>::type Col;
@@ -187,6 +190,7 @@ sweep_kernel(SweepParams<Real> P)
     unsigned char *sMode = reinterpret_cast<unsigned char *>(sQ + 3 * HSZ); // chain mode (see below)
     __shared__ unsigned s_ticket;
     __shared__ volatile int s_ready;             // chunks whose halo is staged
+    __shared__ volatile int s_done;              // chunks the chain has completed
     __shared__ double s_bud[3];
     const HaloList<TX, TY, TZ> &HL = g_halo_list<TX, TY, TZ>;
 
@@ -236,6 +240,7 @@ sweep_kernel(SweepParams<Real> P)
             if (t < (unsigned)P.nitems && P.grids[P.jobs[P.items[t].job].grid].st->done) t |= 0x80000000u;
             s_ticket = t;
             s_ready = 0;
+            s_done = 0;
         }
         __syncthreads();
         const unsigned tk = s_ticket;
@@ -250,7 +255,24 @@ sweep_kernel(SweepParams<Real> P)
         const Real *xin = (P.which == 1) ? G.xh : G.x;
         const Real dx = G.dx, sig = G.sigma0, tau0 = G.tau0;
 
-        if (tid >= NT) {
+        if (tid >= NT + 32) {
+            // ---------------- publisher warp ----------------
+            // progress count after every chunk: planes < m1 done and their face
+            // cells written (the chain's barrier and the shared-memory counter
+            // order those writes before this thread's release)
+            if (tid == NT + 32 && tile_self != P.skip_publish) {
+                int k = 0;
+                for (int m0 = 0; m0 < NP; m0 += chunk, k++) {
+                    long long spins = 0;
+                    while (s_done <= k) {
+                        if (++spins > (P.spin_limit << 4)) { atomicCAS(P.err, 0, (int)DEVERR_TIMEOUT); break; }
+                        if ((spins & 63) == 0) __nanosleep(32);
+                    }
+                    __threadfence_block();
+                    st_release(P.flags + tile_self, (unsigned)min(m0 + chunk, NP));
+                }
+            }
+        } else if (tid >= NT) {
             // ---------------- producer warp ----------------
             const int lane = tid - NT;
             // zero the halo (read as absent until staged)
@@ -550,8 +572,8 @@ sweep_kernel(SweepParams<Real> P)
                     }
                     chain_sync<NT>();
                 }
-                // 3. progress: planes < m1 are done and their face cells written
-                if (tid == 0 && tile_self != P.skip_publish) st_release(P.flags + tile_self, (unsigned)m1);
+                // 3. chunk done: hand its progress to the publisher warp
+                if (tid == 0) { __threadfence_block(); s_done = k + 1; }
             }
 
             // 4. entry columns of the tile's cells
@@ -602,7 +624,7 @@ template <typename Real, int TX, int TY, int TZ, int MODE>
 static cudaError_t launch_shape(const SweepParams<Real> &P, int nblocks, cudaStream_t s)
 {
     constexpr size_t sm = sweep_smem<Real, TX, TY, TZ>();
-    sweep_kernel<Real, TX, TY, TZ, MODE><<<nblocks, TY * TZ + 32, sm, s>>>(P);
+    sweep_kernel<Real, TX, TY, TZ, MODE><<<nblocks, TY * TZ + 64, sm, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -643,8 +665,8 @@ int sweep_occupancy(int shape, int mode)
 #define OOTS_OCC(ID, TX, TY, TZ)                                                                      \
     if (shape == ID) {                                                                                \
         constexpr size_t sm = sweep_smem<Real, TX, TY, TZ>();                                         \
-        if (mode == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 0>, TY * TZ + 32, sm); \
-        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 1>, TY * TZ + 32, sm); \
+        if (mode == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 0>, TY * TZ + 64, sm); \
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 1>, TY * TZ + 64, sm); \
     }
     OOTS_SHAPES(OOTS_OCC)
 #undef OOTS_OCC

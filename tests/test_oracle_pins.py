@@ -452,3 +452,18 @@ def test_paper_numbers():
         t = frac * dxs / (F / n)     # a fraction of the time the front needs to cross the cell
         x, IF, IR, _ = oracle.integrate(1.0, t, 0.0, [(0, A, SIG * n * dxs, 0.0)])
         assert abs((1 - x) * n * dxs / (F * t) - 1) < 1e-12
+
+
+def test_integrate_cells_matches_whole_grid_step():
+    """The selected-cells entry point (used for sampled checks on grids too
+    large to integrate whole) reproduces the A2 substep cell by cell: every
+    cell, in a shuffled order, from the substep's own entry columns."""
+    w = inputs.small_random(n=9, ny=7, nz=8, seed=5, nsrc=2, spectrum="bb")
+    P = oracle.Problem.from_workload(w)
+    x = np.ascontiguousarray(w.x0.reshape(w.nz, w.ny, w.nx).astype(np.float64))
+    x0 = x.copy()
+    dt = 0.01 * w.t_rec
+    _, _, _, N1 = P.substep(x, 0.0, dt, scheme=2, dt_fixed=dt, want_N1=True)
+    idx = np.random.default_rng(3).permutation(P.ncell)
+    xs = P.integrate_cells(idx, x0.ravel()[idx], N1, dt)
+    assert np.array_equal(xs, x.ravel()[idx])
