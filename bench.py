@@ -129,6 +129,44 @@ def job_rate(units_per_rank, world, t_ms):
     return world * units_per_rank / (t_ms / 1e3)
 
 
+KERNEL_SOURCES = ("common.cuh", "integrator.cuh", "kernels.h", "oots_internal.h", "sweep.cu", "cell.cu")
+TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "dram_traffic_lognormal128_mixed.md")
+
+
+def kernel_source_hash():
+    """sha1 over the device sources, to tell whether ncu counters still describe the kernels."""
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1201_5651_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def _traffic(kinds):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch summed over the launch kinds of
+    the dominant kernel, from the committed ncu summary; None when that summary is absent or was
+    taken on other kernel sources."""
+    try:
+        text = open(TRAFFIC_SUMMARY).read()
+    except OSError:
+        return None
+    rows, sha = {}, None
+    for line in text.splitlines():
+        if line.startswith("kernel sources sha1:"):
+            sha = line.split(":", 1)[1].strip().strip("`")
+        cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 3 and cells[0] in ("sweep1", "ratedt", "half", "half_general", "sweep2", "full",
+                                            "full_general"):
+            try:
+                rows[cells[0]] = float(cells[1]) + float(cells[2])
+            except ValueError:
+                pass
+    if sha != kernel_source_hash() or not all(k in rows for k in kinds):
+        return None
+    return sum(rows[k] for k in kinds)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -296,7 +334,9 @@ def run_ours(args, rank, world, local_rank):
         "accuracy_vs_fp64": acc,
         "roofline": {"bound": "hbm", "kernel": dom + (" (closed-form + general pass)" if dom in ("half", "full") else ""),
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_source": peak_src,
+                     "frac": achieved / peak,
+                     "traffic": _traffic([dom, dom + "_general"] if dom in ("half", "full") else [dom]),
+                     "traffic_unit": "bytes per launch (ncu dram read + write, profiles/)", "peak_source": peak_src,
                      "bytes_per_cell": bpc, "step_bytes_per_cell": step_bytes,
                      "step_frac": step_bytes * w.ncell / (t_mixed / args.steps / 1e3) / 1e9 / peak},
         "kernel_ms": prof_avg,

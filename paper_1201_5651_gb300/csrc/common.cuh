@@ -9,6 +9,12 @@
 #include "oots_internal.h"
 
 #define OOTS_HD __host__ __device__
+// one out-of-line copy of a routine called from many sites (instruction-cache footprint)
+#ifdef __CUDACC__
+#define OOTS_NOINLINE __noinline__
+#else
+#define OOTS_NOINLINE __attribute__((noinline))
+#endif
 
 namespace oots {
 
@@ -144,7 +150,7 @@ OOTS_HD __forceinline__ int tab_interval(const DevTable<Real> &T, Real lnN)
 
 // ln(P(N)/Q); -inf above the table.
 template <typename Real>
-OOTS_HD Real tab_lnp(const DevTable<Real> &T, Real N)
+OOTS_HD OOTS_NOINLINE Real tab_lnp(const DevTable<Real> &T, Real N)
 {
     if (N <= Real(0)) return Real(0);
     if (N < T.N0) return m_log1p(-T.a0 * (N / T.N0));
@@ -185,7 +191,7 @@ OOTS_HD __forceinline__ Real tab_dpoly(const Real *a, Real t)
 // table the first and last partial intervals by divided differences and the
 // whole intervals in between by node values.
 template <typename Real>
-OOTS_HD Real tab_dlnp(const DevTable<Real> &T, Real Na, Real dN)
+OOTS_HD OOTS_NOINLINE Real tab_dlnp(const DevTable<Real> &T, Real Na, Real dN)
 {
     if (!(dN > Real(0))) return Real(0);
     if (Na + dN > T.Nhi) return -RealLimits<Real>::inf();
@@ -228,7 +234,7 @@ OOTS_HD Real tab_dlnp(const DevTable<Real> &T, Real Na, Real dN)
 
 // d ln P / d N at N (for the slope of the rate at equilibrium)
 template <typename Real>
-OOTS_HD Real tab_dlnp_dN(const DevTable<Real> &T, Real N)
+OOTS_HD OOTS_NOINLINE Real tab_dlnp_dN(const DevTable<Real> &T, Real N)
 {
     if (N < T.N0) return -T.a0 / (T.N0 - T.a0 * N);
     if (N > T.Nhi) return Real(0);

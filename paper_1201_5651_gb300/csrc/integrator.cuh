@@ -116,7 +116,7 @@ template <typename Real> struct IntResult {
 
 // F(x) and F'(x)
 template <typename Real, int NSMAX = MAX_SRC>
-OOTS_HD void ode_F(const CellODE<Real> &C, Real x, Real *F, Real *dF)
+OOTS_HD OOTS_NOINLINE void ode_F(const CellODE<Real> &C, Real x, Real *F, Real *dF)
 {
     Real s = Real(0), d = Real(0);
     for (int i = 0; i < NSMAX && i < C.ns; i++) {
@@ -147,7 +147,7 @@ template <typename Real> struct SrcEq { Real lne; Real Ne; };
 // forms that keep full relative precision for small |d| and cannot overflow
 // for large |d| (every product below is a transmitted fraction <= 1).
 template <typename Real, int NSMAX = MAX_SRC>
-OOTS_HD Real ode_D(const CellODE<Real> &C, const SrcEq<Real> *Q, Real xe, Real d)
+OOTS_HD OOTS_NOINLINE Real ode_D(const CellODE<Real> &C, const SrcEq<Real> *Q, Real xe, Real d)
 {
     Real s = Real(0);
     const bool tiny = m_abs(d) < RealLimits<Real>::tiny() * Real(1e10);
@@ -239,6 +239,7 @@ OOTS_HD Real newton_root(const CellODE<Real> &C, Real lo, Real hi, Real xk, Real
 // broadcasting the values: a whole warp integrates one cell, a panel costs one
 // evaluation of latency and the root search a scan plus a short polish.
 struct SeqEval {
+    static constexpr bool attenuation = true;    // A1's time-averaged attenuation when b0 > 0
     template <typename Real, int NSMAX>
     OOTS_HD Real root(const CellODE<Real> &C, Real x0, Real f0, Real F0, Real dF0) const
     {
@@ -254,6 +255,7 @@ struct SeqEval {
 };
 #ifdef __CUDACC__
 struct WarpEval {
+    static constexpr bool attenuation = false;   // integration passes only (b0 = 0)
     int lane;
     // Lane l samples f at a point of the bracket, ascending in x with l and
     // geometric towards the end the root lies away from (x for a root below
@@ -593,7 +595,8 @@ OOTS_HD IntResult<Real> integrate_general(const CellODE<Real> &C, Real x0, Real 
     }
     R.x = xe + d0 * m_exp(ustar);
     R.IR = IR;
-    if (C.b0 > Real(0)) R.lnfav = attenuation_average<Real, NSMAX>(C, Q, xe, d0, Dinf, h, ustar, ut, found, wt);
+    if (Eval::attenuation && C.b0 > Real(0))
+        R.lnfav = attenuation_average<Real, NSMAX>(C, Q, xe, d0, Dinf, h, ustar, ut, found, wt);
     return R;
 }
 

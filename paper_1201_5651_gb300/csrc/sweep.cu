@@ -52,6 +52,20 @@ template <int N> __device__ __forceinline__ void chain_sync()
 {
     asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
 }
+// Chunk hand-off from the producer warp to the chain warps: named barrier
+// 2 + k % 14 for chunk k, N = chain threads + 32.  The producer arrives
+// (without waiting) once the chunk's halo is staged; the chain waits on it,
+// blocked in hardware rather than polling.  The barrier orders the
+// producer's shared-memory writes before the chain's reads.
+constexpr int kHandoffBarriers = 14;
+template <int N> __device__ __forceinline__ void chunk_arrive(int k)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(2 + k % kHandoffBarriers), "n"(N) : "memory");
+}
+template <int N> __device__ __forceinline__ void chunk_wait(int k)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(2 + k % kHandoffBarriers), "n"(N) : "memory");
+}
 
 template <typename Col> __device__ __forceinline__ Col ld_face(const Col *p);
 template <> __device__ __forceinline__ double ld_face<double>(const double *p) { return __ldcg(p); }
@@ -189,7 +203,6 @@ sweep_kernel(SweepParams<Real> P)
     Real *sQ = sDI + HSZ;                              // 3 x HSZ neighbour weights (see below)
     unsigned char *sMode = reinterpret_cast<unsigned char *>(sQ + 3 * HSZ); // chain mode (see below)
     __shared__ unsigned s_ticket;
-    __shared__ volatile int s_ready;             // chunks whose halo is staged
     __shared__ volatile int s_done;              // chunks the chain has completed
     __shared__ double s_bud[3];
     const HaloList<TX, TY, TZ> &HL = g_halo_list<TX, TY, TZ>;
@@ -197,7 +210,9 @@ sweep_kernel(SweepParams<Real> P)
     Col *const faceN = reinterpret_cast<Col *>(P.faceN_raw);
     const int tid = threadIdx.x;
     const int clj = tid % TY, clk = tid / TY;    // chain threads: own (j,k) column
-    const int chunk = P.chunk > 0 ? P.chunk : 4;
+    // planes per chunk; at most kHandoffBarriers chunks per tile, so no
+    // hand-off barrier is reused within a tile
+    const int chunk = max(P.chunk > 0 ? P.chunk : 4, (NP + kHandoffBarriers - 1) / kHandoffBarriers);
     double bud_ions = 0.0, bud_rec = 0.0;
     int bud_grid = -1;
 
@@ -239,7 +254,6 @@ sweep_kernel(SweepParams<Real> P)
             // tiles skip, so no wait is left pending)
             if (t < (unsigned)P.nitems && P.grids[P.jobs[P.items[t].job].grid].st->done) t |= 0x80000000u;
             s_ticket = t;
-            s_ready = 0;
             s_done = 0;
         }
         __syncthreads();
@@ -266,7 +280,7 @@ sweep_kernel(SweepParams<Real> P)
                     long long spins = 0;
                     while (s_done <= k) {
                         if (++spins > (P.spin_limit << 4)) { atomicCAS(P.err, 0, (int)DEVERR_TIMEOUT); break; }
-                        if ((spins & 63) == 0) __nanosleep(32);
+                        __nanosleep(64);
                     }
                     __threadfence_block();
                     st_release(P.flags + tile_self, (unsigned)min(m0 + chunk, NP));
@@ -326,7 +340,7 @@ sweep_kernel(SweepParams<Real> P)
                         if (en[u]) { sN[en[u] & 0x3fffu] = vN[u]; sW[en[u] & 0x3fffu] = vW[u]; }
                 }
                 __syncwarp();
-                if (lane == 0) { __threadfence_block(); s_ready = k + 1; }
+                chunk_arrive<NT + 32>(k);
             }
         } else {
             // ---------------- chain warps ----------------
@@ -405,17 +419,9 @@ sweep_kernel(SweepParams<Real> P)
             int k = 0;
             for (int m0 = 0; m0 < NP; m0 += chunk, k++) {
                 const int m1 = min(m0 + chunk, NP);
-                if (tid == 0) {
-                    // the producer always advances (its waits are bounded); this
-                    // bound only guards against a broken invariant
-                    long long spins = 0;
-                    while (s_ready <= k) {
-                        if (++spins > (P.spin_limit << 4)) { atomicCAS(P.err, 0, (int)DEVERR_TIMEOUT); break; }
-                        if ((spins & 255) == 0) __nanosleep(64);
-                    }
-                    __threadfence_block();
-                }
-                chain_sync<NT>();
+                // the chunk's halo is staged (the producer's upstream waits are
+                // bounded, so it always arrives)
+                chunk_wait<NT + 32>(k);
                 // halo-adjacent cells of this chunk: neighbour weights
                 if (MODE == 0) {
                     for (int m = m0; m < m1; m++) {
@@ -452,6 +458,42 @@ sweep_kernel(SweepParams<Real> P)
                                              + sQ[2 * HSZ + h] * ColT<Real>::sub_r(sN[h11], N00);
                                 Nout = ColT<Real>::add(N00, d + dval);
                                 sDI[h] = ColT<Real>::to_real(ColT<Real>::add(N00, d));
+                            } else if (MODE == 0 && (mode & 0x20)) {
+                                // tied dominant axes: the average over the tied axes of
+                                // each axis's normalised interpolation, as weighted
+                                // differences to the a0-1 neighbour of the first tied axis
+                                // (the weights of all terms sum to one)
+                                const int idx[3] = {i, j, k};
+                                const int c2[3] = {2 * i + 1, 2 * j + 1, 2 * k + 1};
+                                const int cm = max(c2[0], max(c2[1], c2[2]));
+                                const int a0 = c2[0] == cm ? 0 : 1;
+                                const Col Nref = sN[h - str_a(a0)];
+                                const Real inv_nt = Real(1) / Real((c2[0] == cm) + (c2[1] == cm) + (c2[2] == cm));
+                                Real d = Real(0);
+#pragma unroll
+                                for (int a = 0; a < 3; a++) {
+                                    if (c2[a] != cm) continue;
+                                    const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+                                    const int ha = h - str_a(a), s1 = str_t1(a), s2 = str_t2(a);
+                                    const Real w1 = Real(c2[t1]) / Real(c2[a]);   // weight of the t1-1 neighbour
+                                    const Real w2 = Real(c2[t2]) / Real(c2[a]);
+                                    Real wv[4], dv[4], ws = Real(0);
+#pragma unroll
+                                    for (int e = 0; e < 4; e++) {
+                                        const int e1 = e & 1, e2 = e >> 1;
+                                        const bool ok = idx[t1] - e1 >= 0 && idx[t2] - e2 >= 0;
+                                        const int hn = ha - (e1 ? s1 : 0) - (e2 ? s2 : 0);
+                                        wv[e] = ok ? (e1 ? w1 : Real(1) - w1) * (e2 ? w2 : Real(1) - w2) * sW[hn] : Real(0);
+                                        dv[e] = ok ? ColT<Real>::sub_r(sN[hn], Nref) : Real(0);
+                                        ws += wv[e];
+                                    }
+                                    if (ws > Real(0)) {
+                                        const Real r = inv_nt / ws;
+                                        d += r * (wv[0] * dv[0] + wv[1] * dv[1] + wv[2] * dv[2] + wv[3] * dv[3]);
+                                    }
+                                }
+                                Nout = ColT<Real>::add(Nref, d + dval);
+                                sDI[h] = ColT<Real>::to_real(ColT<Real>::add(Nref, d));
                             } else {
                                 Col Nin = ColT<Real>::zero();
                                 if (!(mode & 0x30)) {
