@@ -262,8 +262,8 @@ int oots_debug_set(oots_ctx *ctx, int key, long long value);
  * (float buffers).  The call enqueues on `stream` (NULL: the default stream)
  * and returns when the trace has finished.
  *
- * Nothing is allocated: the scratch (tile work list, tile flags, published
- * tile faces, descriptors) is one 32 MiB static device array that every GPU
+ * Nothing is allocated: the scratch (tile work list, published tile faces,
+ * descriptors) is one 64 MiB static device array that every GPU
  * loading the library holds until the process exits.  A grid that needs more
  * tiles of 16x8x8 cells than fit in it (about 5400 in FP64, 7200 mixed, i.e.
  * roughly 5 million cells) is rejected with OOTS_E_INVAL, *status_detail

@@ -175,14 +175,17 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
 }
 
 // General pass: one warp per queued cell (HALF: queue 0, FULL: queue 1).
+// Warps take the next queued cell from a head counter (qcount[2 + queue]), so
+// the pass ends when the cells run out rather than when the warp that drew
+// the slowest share finishes.
 // Every lane forms the same rates and runs the same root search; the
 // quadrature nodes are spread over the lanes (WarpEval).  Budget sums of FULL
 // are gathered per block in shared memory for up to eight grids and flushed
 // with one atomic per grid and block.
 template <typename Real, int OP, int NSMAX>
-__global__ void __launch_bounds__(256) cell_general_kernel(const GridDev<Real> *grids, int ngrid, const long long *offsets,
-                                                           const DevTable<Real> *tabs, const unsigned *queue,
-                                                           const unsigned *qcount)
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2)
+cell_general_kernel(const GridDev<Real> *grids, int ngrid, const long long *offsets, const DevTable<Real> *tabs,
+                    const unsigned *queue, unsigned *qcount)
 {
     __shared__ double s_ions[8], s_rec[8];
     __shared__ int s_gid[8];
@@ -191,9 +194,13 @@ __global__ void __launch_bounds__(256) cell_general_kernel(const GridDev<Real> *
         if (threadIdx.x < 8) { s_ions[threadIdx.x] = 0.0; s_rec[threadIdx.x] = 0.0; s_gid[threadIdx.x] = -1; }
         __syncthreads();
     }
-    const unsigned nq = qcount[OP == OP_HALF ? 0 : 1];
-    const unsigned nw = (gridDim.x * blockDim.x) >> 5;
-    for (unsigned q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < nq; q += nw) {
+    const int qi = OP == OP_HALF ? 0 : 1;
+    const unsigned nq = qcount[qi];
+    for (;;) {
+        unsigned q = 0;
+        if (lane == 0) q = atomicAdd(&qcount[2 + qi], 1u);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= nq) break;
         const long long idx = queue[q];
         const int gi = find_grid(offsets, ngrid, idx);
         const GridDev<Real> &G = grids[gi];
@@ -255,7 +262,7 @@ template <typename Real>
 __global__ void finalize_kernel(const GridDev<Real> *grids, int ngrid, int stage, unsigned *qcount)
 {
     const int gi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (stage == 0 && gi == 0) { qcount[0] = 0u; qcount[1] = 0u; }
+    if (stage == 0 && gi == 0) { qcount[0] = 0u; qcount[1] = 0u; qcount[2] = 0u; qcount[3] = 0u; }
     if (gi >= ngrid) return;
     DevState *st = grids[gi].st;
     if (stage == 0) {

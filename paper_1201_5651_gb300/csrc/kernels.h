@@ -28,15 +28,18 @@ template <typename Real> struct SweepParams {
     int nitems;
     int which;                         // 0: trace x into N1; 1: trace xh into N2
     unsigned *ticket;                  // zeroed before each launch
-    unsigned *flags;                   // one per tile, zeroed before each launch
-    void *faceN_raw;                   // per tile 3 faces x FMAX columns
-    Real *faceW;                       // per tile 3 faces x FMAX weight factors
+    unsigned *done;                    // CTAs finished; zeroed before each launch
+    unsigned *epoch;                   // launches finished so far (persistent; starts at 0)
+    unsigned long long *faces;         // per tile 3 faces x FMAX cells x tagged words (zeroed once)
     const DevTable<Real> *tabs;
     int *err;                          // sticky device error
     long long spin_limit;              // bounded wait on upstream tiles
-    long long skip_publish;            // tile that never publishes (fault-injection test), -1: none
-    int chunk;                         // planes per published progress step (<= 0: 4)
+    long long skip_publish;            // tile that never writes its faces (fault-injection test), -1: none
+    int chunk;                         // planes per hand-off chunk (<= 0: 4)
 };
+
+// tagged 8-byte words per published face cell (mixed path 3, FP64 path 4)
+template <typename Real> constexpr int face_words() { return sizeof(Real) == 4 ? 3 : 4; }
 
 template <typename Real> cudaError_t prepare_sweeps();
 template <typename Real> int sweep_occupancy(int shape, int mode);   // resident CTAs per SM
@@ -52,7 +55,7 @@ cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *
                         const DevTable<Real> *tabs, int op, int nsmax, unsigned *queue, unsigned *qcount,
                         int gen_blocks, cudaStream_t s);
 template <typename Real> int cell_general_occupancy(int nsmax);
-// stage 0 also clears the two queue counters
+// stage 0 also clears the queue lengths and the general passes' head counters
 template <typename Real>
 cudaError_t launch_finalize(const GridDev<Real> *grids, int ngrid, int stage, unsigned *qcount, cudaStream_t s);
 

@@ -1,7 +1,7 @@
 // oots_trace_noalloc: the column-density trace for callers that cannot
 // allocate device memory.  It runs the same wavefront sweep kernel as the
 // context API, but every piece of scratch it needs (the tile work list, the
-// tile flags, the published tile faces and the small descriptors) lives in
+// published tile faces and the small descriptors) lives in
 // one file-scope static device array, so the call makes no cudaMalloc, no
 // cudaFree and no heap allocation on the host.
 #include <cmath>
@@ -21,8 +21,8 @@ void oots_set_error_text(const char *msg);
 
 namespace {
 
-// 32 MiB, resident on every device that loads the library until the process exits.
-constexpr size_t kScratchBytes = (size_t)32 << 20;
+// 64 MiB, resident on every device that loads the library until the process exits.
+constexpr size_t kScratchBytes = (size_t)64 << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kShape = 0;                       // tile shape 16 x 8 x 8
@@ -32,7 +32,8 @@ constexpr int kMaxDiag = 4096;                  // tile diagonals the work-list 
 constexpr size_t kHeader = 64 * 1024;           // ticket, error, state, counters
 
 // header layout (byte offsets inside the scratch)
-constexpr size_t kOffTicket = 0;
+constexpr size_t kOffTicket = 0;                // ticket, then the count of finished CTAs
+constexpr size_t kOffEpoch = 64;                // sweep launches so far: never cleared (faces carry it)
 constexpr size_t kOffErr = 128;
 constexpr size_t kOffState = 256;               // DevState (done = 0 after the clear)
 constexpr size_t kOffCount = 1024;              // kMaxDiag unsigned: tiles per diagonal, then cursor
@@ -48,7 +49,7 @@ static DevSetup g_setup[64];
 
 template <typename Real> size_t tile_bytes()
 {
-    return sizeof(TileItem) + sizeof(unsigned) + 3 * kFMAX * (sizeof(Real) + sizeof(typename ColT<Real>::type));
+    return sizeof(TileItem) + 3 * kFMAX * face_words<Real>() * sizeof(unsigned long long);
 }
 
 // One block orders the tiles of the (at most 8) octant jobs by tile diagonal:
@@ -133,13 +134,7 @@ int trace_noalloc(DevSetup &S, int nx, int ny, int nz, double dx, const void *n_
     TileItem *items = (TileItem *)(sc + off);
     off += (size_t)(max_tiles + 1) * sizeof(TileItem);
     off = (off + 255) / 256 * 256;
-    unsigned *flags = (unsigned *)(sc + off);
-    off += (size_t)(max_tiles + 1) * sizeof(unsigned);
-    off = (off + 255) / 256 * 256;
-    Real *faceW = (Real *)(sc + off);
-    off += (size_t)(max_tiles + 1) * 3 * kFMAX * sizeof(Real);
-    off = (off + 255) / 256 * 256;
-    void *faceN = sc + off;
+    unsigned long long *faces = (unsigned long long *)(sc + off);   // zero at load; launches tag epochs 1, 2, ...
 
     GridDev<Real> G;
     memset(&G, 0, sizeof(G));
@@ -158,9 +153,10 @@ int trace_noalloc(DevSetup &S, int nx, int ny, int nz, double dx, const void *n_
     G.tab[0] = -1;
     G.st = (DevState *)(sc + kOffState);
 
-    // clear what must start at zero: ticket, error, device state, flags
-    if (cudaMemsetAsync(sc, 0, kOffCount, st) != cudaSuccess) return -1;
-    if (cudaMemsetAsync(flags, 0, (size_t)tiles * sizeof(unsigned), st) != cudaSuccess) return -1;
+    // clear what must start at zero: ticket, finished-CTA count, error, device state
+    // (the epoch and the faces are never cleared: stale face words carry older epochs)
+    if (cudaMemsetAsync(sc + kOffTicket, 0, kOffEpoch - kOffTicket, st) != cudaSuccess) return -1;
+    if (cudaMemsetAsync(sc + kOffErr, 0, kOffCount - kOffErr, st) != cudaSuccess) return -1;
     if (cudaMemcpyAsync(sc + kOffJobs, jobs, njobs * sizeof(Job), cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
     if (cudaMemcpyAsync(sc + kOffGrid, &G, sizeof(G), cudaMemcpyHostToDevice, st) != cudaSuccess) return -1;
     if (tiles == 0) return 0;
@@ -175,9 +171,9 @@ int trace_noalloc(DevSetup &S, int nx, int ny, int nz, double dx, const void *n_
     P.nitems = (int)tiles;
     P.which = 0;
     P.ticket = (unsigned *)(sc + kOffTicket);
-    P.flags = flags;
-    P.faceN_raw = faceN;
-    P.faceW = faceW;
+    P.done = (unsigned *)(sc + kOffTicket) + 1;
+    P.epoch = (unsigned *)(sc + kOffEpoch);
+    P.faces = faces;
     P.tabs = nullptr;
     P.err = (int *)(sc + kOffErr);
     P.spin_limit = 1ll << 22;

@@ -129,10 +129,8 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     TileItem *d_items = nullptr;
     int nitems = 0;
     long long ntiles = 0;
-    unsigned char *d_sync = nullptr;   // ticket (first 128 bytes) + flags
-    size_t sync_bytes = 0;
-    void *d_faceN = nullptr;
-    Real *d_faceW = nullptr;
+    unsigned *d_sync = nullptr;        // [0] ticket, [1] done (zeroed per sweep), [16] epoch (persistent)
+    unsigned long long *d_faces = nullptr;
     DevTable<Real> *d_tabs = nullptr;
     std::vector<void *> tabmem;
     long long *d_offsets = nullptr;
@@ -157,8 +155,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         cudaFree(d_jobs);
         cudaFree(d_items);
         cudaFree(d_sync);
-        cudaFree(d_faceN);
-        cudaFree(d_faceW);
+        cudaFree(d_faces);
         cudaFree(d_tabs);
         for (void *p : tabmem) cudaFree(p);
         cudaFree(d_offsets);
@@ -306,11 +303,12 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
             CU(cudaMemcpy(d_jobs, jobs.data(), jobs.size() * sizeof(Job), cudaMemcpyHostToDevice));
             CU(cudaMalloc(&d_items, items.size() * sizeof(TileItem)));
             CU(cudaMemcpy(d_items, items.data(), items.size() * sizeof(TileItem), cudaMemcpyHostToDevice));
-            sync_bytes = 128 + (size_t)ntiles * sizeof(unsigned);
-            CU(cudaMalloc(&d_sync, sync_bytes));
-            const size_t colsz = sizeof(typename ColT<Real>::type);
-            CU(cudaMalloc(&d_faceN, (size_t)ntiles * 3 * FMAX * colsz));
-            CU(cudaMalloc(&d_faceW, (size_t)ntiles * 3 * FMAX * sizeof(Real)));
+            CU(cudaMalloc(&d_sync, 128));
+            CU(cudaMemset(d_sync, 0, 128));
+            // faces start with epoch 0 in every word; launches use epochs 1, 2, ...
+            const size_t fbytes = (size_t)ntiles * 3 * FMAX * face_words<Real>() * sizeof(unsigned long long);
+            CU(cudaMalloc(&d_faces, fbytes));
+            CU(cudaMemset(d_faces, 0, fbytes));
         }
         if (!tabs.empty()) {
             CU(cudaMalloc(&d_tabs, tabs.size() * sizeof(DevTable<Real>)));
@@ -332,10 +330,10 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         P.items = d_items;
         P.nitems = nitems;
         P.which = which;
-        P.ticket = (unsigned *)d_sync;
-        P.flags = (unsigned *)(d_sync + 128);
-        P.faceN_raw = d_faceN;
-        P.faceW = d_faceW;
+        P.ticket = d_sync;
+        P.done = d_sync + 1;
+        P.epoch = d_sync + 16;
+        P.faces = d_faces;
         P.tabs = d_tabs;
         P.err = d_err;
         P.spin_limit = spin_limit;
@@ -347,7 +345,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     int sweep(cudaStream_t s, int which, int mode)
     {
         if (nitems == 0) return OOTS_OK;
-        CU(cudaMemsetAsync(d_sync, 0, sync_bytes, s));
+        CU(cudaMemsetAsync(d_sync, 0, 2 * sizeof(unsigned), s));   // ticket and done; the epoch persists
         if (prof) prof->mark(0);
         CU(launch_sweep<Real>(params(which), shape, mode, mode == 0 ? nblocks0 : nblocks1, s));
         if (prof) prof->mark(mode == 1 ? OOTS_K_IMPLICIT : (which == 0 ? OOTS_K_SWEEP1 : OOTS_K_SWEEP2));

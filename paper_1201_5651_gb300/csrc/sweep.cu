@@ -10,23 +10,23 @@
 // tile was claimed by a running CTA before any tile that waits for it.
 //
 // Inside a tile the cells are processed plane by plane (li+lj+lk = m, one
-// chain thread per (j,k) column).  The tiles are pipelined: a tile publishes
-// a progress count (planes done) after every chunk of planes, and its three
-// downstream faces are written to global memory as their cells complete, so
-// a downstream tile starts as soon as the planes it needs exist instead of
-// after the whole upstream tile.  Plane m of a tile reads the face of its
-// upstream tile along axis a at that tile's plane m + T_a - 1; edge and corner
-// halo cells are covered by transitivity (the face-adjacent upstream tile
-// waited for them before it completed the plane we wait for).
+// chain thread per (j,k) column).  The tiles are pipelined: a tile writes
+// the cells of its three downstream faces to global memory as they complete,
+// and a downstream tile starts each chunk of planes as soon as the face cells
+// that chunk reads exist, instead of after the whole upstream tile.
 //
-// Each CTA holds the chain warps, one producer warp and one publisher warp.
-// The publisher turns the chain's per-chunk completion (a shared-memory
-// counter) into the GPU-scope release of the tile's progress, so the release
-// fence never stalls the chain.  The producer waits
-// (bounded spin, acquire) for the upstream progress each chunk needs and
-// stages that chunk's halo cells (a compile-time list sorted by the first
-// plane that reads them) from the published faces into shared memory, running
-// ahead of the chain.  The chain warps form each cell's normalised neighbour
+// Hand-off without flags or fences: every published face cell is a few
+// 8-byte words, each holding 4 bytes of the value and the 32-bit epoch of
+// the launch (aligned 8-byte accesses are single-copy atomic).  A reader
+// polls the words of the cells it needs until every one carries the current
+// epoch, so each word validates itself and no progress counter, release
+// fence or acquire is needed.  The epoch advances once per launch (the last
+// CTA to finish stores it), so words left by earlier launches never match.
+//
+// Each CTA holds the chain warps and one producer warp.  The producer stages
+// each chunk's halo cells (a compile-time list sorted by the first plane that
+// reads them) from the upstream faces into shared memory, with bounded
+// polling, running ahead of the chain.  The chain warps form each cell's normalised neighbour
 // weights off the critical path (interior cells before the first wait,
 // halo-adjacent cells once their chunk's halo is staged), so a plane costs
 // one weighted difference sum and one column add.  Shared-memory rows are
@@ -37,15 +37,19 @@
 
 namespace oots {
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+__device__ __forceinline__ unsigned long long ld_word(const unsigned long long *p)
 {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+__device__ __forceinline__ void st_word(unsigned long long *p, unsigned long long v)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long tagged(unsigned bits, unsigned epoch)
+{
+    return ((unsigned long long)epoch << 32) | bits;
 }
 // barrier among the chain warps only (the producer warp does not take part)
 template <int N> __device__ __forceinline__ void chain_sync()
@@ -67,19 +71,45 @@ template <int N> __device__ __forceinline__ void chunk_wait(int k)
     asm volatile("bar.sync %0, %1;" ::"r"(2 + k % kHandoffBarriers), "n"(N) : "memory");
 }
 
-template <typename Col> __device__ __forceinline__ Col ld_face(const Col *p);
-template <> __device__ __forceinline__ double ld_face<double>(const double *p) { return __ldcg(p); }
-template <> __device__ __forceinline__ ff ld_face<ff>(const ff *p)
-{
-    float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
-    return ff{v.x, v.y};
-}
-template <typename Col> __device__ __forceinline__ void st_face(Col *p, Col v);
-template <> __device__ __forceinline__ void st_face<double>(double *p, double v) { __stcg(p, v); }
-template <> __device__ __forceinline__ void st_face<ff>(ff *p, ff v)
-{
-    __stcg(reinterpret_cast<float2 *>(p), make_float2(v.hi, v.lo));
-}
+// A published face cell (column N_out and weight factor W) as tagged words:
+// mixed path {N.hi}, {N.lo}, {W}; FP64 path both halves of N and of W.
+template <typename Real> struct FaceWords;
+template <> struct FaceWords<float> {
+    enum { W = 3 };
+    static __device__ __forceinline__ void store(unsigned long long *p, ff N, float w, unsigned e)
+    {
+        st_word(p + 0, tagged(__float_as_uint(N.hi), e));
+        st_word(p + 1, tagged(__float_as_uint(N.lo), e));
+        st_word(p + 2, tagged(__float_as_uint(w), e));
+    }
+    // true once every word carries epoch e
+    static __device__ __forceinline__ bool load(const unsigned long long *p, unsigned e, ff &N, float &w)
+    {
+        const unsigned long long a = ld_word(p + 0), b = ld_word(p + 1), c = ld_word(p + 2);
+        N = ff{__uint_as_float((unsigned)a), __uint_as_float((unsigned)b)};
+        w = __uint_as_float((unsigned)c);
+        return (unsigned)(a >> 32) == e && (unsigned)(b >> 32) == e && (unsigned)(c >> 32) == e;
+    }
+};
+template <> struct FaceWords<double> {
+    enum { W = 4 };
+    static __device__ __forceinline__ void store(unsigned long long *p, double N, double w, unsigned e)
+    {
+        const unsigned long long n = (unsigned long long)__double_as_longlong(N), v = (unsigned long long)__double_as_longlong(w);
+        st_word(p + 0, tagged((unsigned)n, e));
+        st_word(p + 1, tagged((unsigned)(n >> 32), e));
+        st_word(p + 2, tagged((unsigned)v, e));
+        st_word(p + 3, tagged((unsigned)(v >> 32), e));
+    }
+    static __device__ __forceinline__ bool load(const unsigned long long *p, unsigned e, double &N, double &w)
+    {
+        const unsigned long long a = ld_word(p + 0), b = ld_word(p + 1), c = ld_word(p + 2), d = ld_word(p + 3);
+        N = __longlong_as_double((long long)(((b & 0xffffffffull) << 32) | (a & 0xffffffffull)));
+        w = __longlong_as_double((long long)(((d & 0xffffffffull) << 32) | (c & 0xffffffffull)));
+        return (unsigned)(a >> 32) == e && (unsigned)(b >> 32) == e && (unsigned)(c >> 32) == e &&
+               (unsigned)(d >> 32) == e;
+    }
+};
 
 // Shared-memory layout of a sweep tile: a one-cell halo on the three upstream
 // sides, with the row strides padded so that the cells of one plane
@@ -182,7 +212,7 @@ template <int TX, int TY, int TZ>
 __device__ const HaloList<TX, TY, TZ> g_halo_list = make_halo_list<TX, TY, TZ>();
 
 template <typename Real, int TX, int TY, int TZ, int MODE>
-__global__ void __launch_bounds__(TY *TZ + 64)
+__global__ void __launch_bounds__(TY *TZ + 32)
 sweep_kernel(SweepParams<Real> P)
 {
     typedef typename ColT<Real>::type Col;
@@ -203,11 +233,14 @@ sweep_kernel(SweepParams<Real> P)
     Real *sQ = sDI + HSZ;                              // 3 x HSZ neighbour weights (see below)
     unsigned char *sMode = reinterpret_cast<unsigned char *>(sQ + 3 * HSZ); // chain mode (see below)
     __shared__ unsigned s_ticket;
-    __shared__ volatile int s_done;              // chunks the chain has completed
     __shared__ double s_bud[3];
     const HaloList<TX, TY, TZ> &HL = g_halo_list<TX, TY, TZ>;
 
-    Col *const faceN = reinterpret_cast<Col *>(P.faceN_raw);
+    typedef FaceWords<Real> FW;
+    unsigned long long *const faces = P.faces;
+    // the epoch of this launch: one past the last finished launch's (read
+    // before this CTA reports done, so before the last CTA advances it)
+    const unsigned epoch = *(volatile unsigned *)P.epoch + 1u;
     const int tid = threadIdx.x;
     const int clj = tid % TY, clk = tid / TY;    // chain threads: own (j,k) column
     // planes per chunk; at most kHandoffBarriers chunks per tile, so no
@@ -254,7 +287,6 @@ sweep_kernel(SweepParams<Real> P)
             // tiles skip, so no wait is left pending)
             if (t < (unsigned)P.nitems && P.grids[P.jobs[P.items[t].job].grid].st->done) t |= 0x80000000u;
             s_ticket = t;
-            s_done = 0;
         }
         __syncthreads();
         const unsigned tk = s_ticket;
@@ -269,24 +301,7 @@ sweep_kernel(SweepParams<Real> P)
         const Real *xin = (P.which == 1) ? G.xh : G.x;
         const Real dx = G.dx, sig = G.sigma0, tau0 = G.tau0;
 
-        if (tid >= NT + 32) {
-            // ---------------- publisher warp ----------------
-            // progress count after every chunk: planes < m1 done and their face
-            // cells written (the chain's barrier and the shared-memory counter
-            // order those writes before this thread's release)
-            if (tid == NT + 32 && tile_self != P.skip_publish) {
-                int k = 0;
-                for (int m0 = 0; m0 < NP; m0 += chunk, k++) {
-                    long long spins = 0;
-                    while (s_done <= k) {
-                        if (++spins > (P.spin_limit << 4)) { atomicCAS(P.err, 0, (int)DEVERR_TIMEOUT); break; }
-                        __nanosleep(64);
-                    }
-                    __threadfence_block();
-                    st_release(P.flags + tile_self, (unsigned)min(m0 + chunk, NP));
-                }
-            }
-        } else if (tid >= NT) {
+        if (tid >= NT) {
             // ---------------- producer warp ----------------
             const int lane = tid - NT;
             // zero the halo (read as absent until staged)
@@ -301,24 +316,13 @@ sweep_kernel(SweepParams<Real> P)
             int k = 0;
             for (int m0 = 0; m0 < NP; m0 += chunk, k++) {
                 const int m1 = min(m0 + chunk, NP);
-                // wait: lane a polls the face-adjacent upstream tile along axis a
-                if (lane < 3 && (have & (1u << lane))) {
-                    const long long up = tile_self - (lane == 0 ? sx : (lane == 1 ? sy : sz));
-                    const unsigned need = (unsigned)min(NP, m1 - 1 + (lane == 0 ? TX : (lane == 1 ? TY : TZ)));
-                    long long spins = 0;
-                    unsigned ns = 32;
-                    while (ld_acquire(P.flags + up) < need) {
-                        if (++spins > P.spin_limit) { atomicCAS(P.err, 0, (int)DEVERR_TIMEOUT); break; }
-                        if ((spins & 31) == 0 && *(volatile int *)P.err != 0) break;   // another tile gave up
-                        __nanosleep(ns);
-                        if (ns < 256) ns <<= 1;
-                    }
-                }
-                __syncwarp();
-                // stage the halo cells first read by planes [m0, m1), four per lane in flight
+                // stage the halo cells first read by planes [m0, m1), four per lane
+                // in flight, polling each until all its words carry this epoch
                 const int b1 = HL.start[m1];
                 for (int base = HL.start[m0] + lane; base < b1; base += 128) {
                     unsigned en[4];
+                    long long o[4];
+                    bool ok[4];
                     Col vN[4];
                     Real vW[4];
 #pragma unroll
@@ -326,18 +330,33 @@ sweep_kernel(SweepParams<Real> P)
                         const int q = base + 32 * u;
                         en[u] = q < b1 ? __ldg(&HL.e[q]) : 0u;
                         const unsigned mask = en[u] >> 28;
+                        ok[u] = true;
+                        o[u] = 0;
                         if (q < b1 && (mask & ~have) == 0) {
                             const long long src = tile_self - ((mask & 1) ? sx : 0) - ((mask & 2) ? sy : 0) - ((mask & 4) ? sz : 0);
-                            const long long o = src * 3 * FMAX + (long long)((en[u] >> 26) & 3u) * FMAX + ((en[u] >> 14) & 0xfffu);
-                            vN[u] = ld_face<Col>(faceN + o);
-                            vW[u] = __ldcg(P.faceW + o);
+                            o[u] = ((src * 3 + (long long)((en[u] >> 26) & 3u)) * FMAX + ((en[u] >> 14) & 0xfffu)) * FW::W;
+                            ok[u] = FW::load(faces + o[u], epoch, vN[u], vW[u]);
                         } else {
-                            en[u] = 0u;
+                            en[u] = 0u;           // no upstream tile: the cell stays absent
                         }
+                    }
+                    long long spins = 0;
+                    unsigned ns = 32;
+                    while (!(ok[0] && ok[1] && ok[2] && ok[3])) {
+                        if (++spins > P.spin_limit) { atomicCAS(P.err, 0, (int)DEVERR_TIMEOUT); break; }
+                        if ((spins & 31) == 0 && *(volatile int *)P.err != 0) break;   // another tile gave up
+                        __nanosleep(ns);
+                        if (ns < 256) ns <<= 1;
+#pragma unroll
+                        for (int u = 0; u < 4; u++)
+                            if (!ok[u]) ok[u] = FW::load(faces + o[u], epoch, vN[u], vW[u]);
                     }
 #pragma unroll
                     for (int u = 0; u < 4; u++)
-                        if (en[u]) { sN[en[u] & 0x3fffu] = vN[u]; sW[en[u] & 0x3fffu] = vW[u]; }
+                        if (en[u]) {
+                            sN[en[u] & 0x3fffu] = ok[u] ? vN[u] : ColT<Real>::zero();
+                            sW[en[u] & 0x3fffu] = ok[u] ? vW[u] : Real(0);
+                        }
                 }
                 __syncwarp();
                 chunk_arrive<NT + 32>(k);
@@ -415,7 +434,8 @@ sweep_kernel(SweepParams<Real> P)
                 }
             }
 
-            const long long fbase = tile_self * 3 * FMAX;
+            unsigned long long *const fbase = faces + tile_self * 3 * FMAX * FW::W;
+            const bool publish = tile_self != P.skip_publish;
             int k = 0;
             for (int m0 = 0; m0 < NP; m0 += chunk, k++) {
                 const int m1 = min(m0 + chunk, NP);
@@ -599,23 +619,14 @@ sweep_kernel(SweepParams<Real> P)
                             sN[h] = Nout;
                         }
                         // downstream faces are published as their cells complete
-                        if (li == TX - 1) {
-                            st_face<Col>(faceN + fbase + 0 * FMAX + lk * TY + lj, Nout);
-                            __stcg(P.faceW + fbase + 0 * FMAX + lk * TY + lj, wout);
-                        }
-                        if (lj == TY - 1) {
-                            st_face<Col>(faceN + fbase + 1 * FMAX + lk * TX + li, Nout);
-                            __stcg(P.faceW + fbase + 1 * FMAX + lk * TX + li, wout);
-                        }
-                        if (lk == TZ - 1) {
-                            st_face<Col>(faceN + fbase + 2 * FMAX + lj * TX + li, Nout);
-                            __stcg(P.faceW + fbase + 2 * FMAX + lj * TX + li, wout);
+                        if (publish) {
+                            if (li == TX - 1) FW::store(fbase + (0 * FMAX + lk * TY + lj) * FW::W, Nout, wout, epoch);
+                            if (lj == TY - 1) FW::store(fbase + (1 * FMAX + lk * TX + li) * FW::W, Nout, wout, epoch);
+                            if (lk == TZ - 1) FW::store(fbase + (2 * FMAX + lj * TX + li) * FW::W, Nout, wout, epoch);
                         }
                     }
                     chain_sync<NT>();
                 }
-                // 3. chunk done: hand its progress to the publisher warp
-                if (tid == 0) { __threadfence_block(); s_done = k + 1; }
             }
 
             // 4. entry columns of the tile's cells
@@ -651,6 +662,8 @@ sweep_kernel(SweepParams<Real> P)
             atomicAdd(&st->bud_step[1], s_bud[0] + s_bud[1]);
         }
     }
+    // the last CTA to finish advances the epoch for the next launch
+    if (tid == 0 && atomicAdd(P.done, 1u) == gridDim.x - 1) *(volatile unsigned *)P.epoch = epoch;
 }
 
 // ---------------------------------------------------------------------------
@@ -666,7 +679,7 @@ template <typename Real, int TX, int TY, int TZ, int MODE>
 static cudaError_t launch_shape(const SweepParams<Real> &P, int nblocks, cudaStream_t s)
 {
     constexpr size_t sm = sweep_smem<Real, TX, TY, TZ>();
-    sweep_kernel<Real, TX, TY, TZ, MODE><<<nblocks, TY * TZ + 64, sm, s>>>(P);
+    sweep_kernel<Real, TX, TY, TZ, MODE><<<nblocks, TY * TZ + 32, sm, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -707,8 +720,8 @@ int sweep_occupancy(int shape, int mode)
 #define OOTS_OCC(ID, TX, TY, TZ)                                                                      \
     if (shape == ID) {                                                                                \
         constexpr size_t sm = sweep_smem<Real, TX, TY, TZ>();                                         \
-        if (mode == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 0>, TY * TZ + 64, sm); \
-        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 1>, TY * TZ + 64, sm); \
+        if (mode == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 0>, TY * TZ + 32, sm); \
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 1>, TY * TZ + 32, sm); \
     }
     OOTS_SHAPES(OOTS_OCC)
 #undef OOTS_OCC
