@@ -72,6 +72,7 @@ class Clocks:
 
     def __init__(self, index):
         self.proc = None
+        self.skip = 0
         self.index = index
         self.out = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
 
@@ -80,8 +81,19 @@ class Clocks:
             os.makedirs(os.path.dirname(self.out), exist_ok=True)
             self.fh = open(self.out, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
+            # wait for the sampler's first line, then count only the lines that
+            # arrive from here on (the timed region starts right after this)
+            t0 = time.time()
+            self.skip = 0
+            while time.time() - t0 < 5.0:
+                self.fh.flush()
+                n = sum(1 for _ in open(self.out))
+                if n > 0:
+                    self.skip = n
+                    break
+                time.sleep(0.02)
         except Exception:
             self.proc = None
 
@@ -96,7 +108,9 @@ class Clocks:
         self.fh.close()
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.out):
+        for i, line in enumerate(open(self.out)):
+            if i < self.skip:
+                continue
             p = [q.strip() for q in line.split(",")]
             if len(p) < 8:
                 continue
@@ -401,7 +415,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lognormal128_bb")

@@ -303,6 +303,54 @@ struct WarpEval {
 };
 #endif
 
+// Per-source values at the root x_eq and the slope there: Dinf = -f'(x_eq),
+// and bmax, the largest optical depth scale per unit x (the rate bends on
+// |d| ~ 1/bmax).
+template <typename Real, int NSMAX>
+OOTS_HD void root_slope(const CellODE<Real> &C, Real xe, Real sigma0, SrcEq<Real> *Q, Real &Dinf, Real &bmax)
+{
+    bmax = Real(0);
+    Dinf = Real(2) * C.c * (Real(1) - xe);
+    for (int i = 0; i < NSMAX && i < C.ns; i++) {
+        const SrcRate<Real> &r = C.r[i];
+        Q[i].lne = -RealLimits<Real>::inf();
+        Q[i].Ne = Real(0);
+        if (!(r.A > Real(0))) continue;
+        if (r.tab < 0) {
+            Q[i].lne = -r.b * xe;
+            Dinf += r.A * r.b * m_exp(Q[i].lne);
+            bmax = m_max(bmax, r.b);
+        } else {
+            const DevTable<Real> &T = C.tabs[r.tab];
+            Q[i].Ne = r.Nin + r.b * xe;
+            Q[i].lne = m_log(r.p) + tab_dlnp(T, r.Nin, r.b * xe);
+            Real pe = m_exp(Q[i].lne);
+            if (pe > Real(0)) Dinf += -r.A * pe * r.b * tab_dlnp_dN(T, Q[i].Ne);
+            bmax = m_max(bmax, sigma0 * r.b);
+        }
+    }
+}
+
+// Already next to the root (|d0| = |x0 - x_eq| far below both bending scales):
+// the linearised solution about x_eq, d(t) = d0 e^{-Dinf t}.  Returns false
+// when the state is not that close.
+template <typename Real>
+OOTS_HD bool near_root_solution(const CellODE<Real> &C, Real xe, Real d0, Real Dinf, Real bmax, Real h,
+                                IntResult<Real> &R)
+{
+    const Real ad0 = m_abs(d0);
+    if (!(bmax * ad0 <= IntCfg<Real>::zlin() && ad0 <= IntCfg<Real>::zlin() * (Real(1) - xe) && C.b0 == Real(0)))
+        return false;
+    const Real e = m_exp(-Dinf * h);
+    R.x = xe + d0 * e;
+    const Real one = Real(1) - xe;
+    // int c (1 - xe - d)^2 dt = c one^2 h - 2 c one d0 (1 - e)/Dinf + c d0^2 (1 - e^2)/(2 Dinf)
+    const Real g1 = (Dinf * h > Real(1e-6)) ? -m_expm1(-Dinf * h) / Dinf : h;
+    const Real g2 = (Dinf * h > Real(1e-6)) ? -m_expm1(Real(-2) * Dinf * h) / (Real(2) * Dinf) : h;
+    R.IR = C.c * (one * one * h - Real(2) * one * d0 * g1 + d0 * d0 * g2);
+    return true;
+}
+
 // First part of the integration: the closed forms.  Returns true when the
 // cell is done (photon-free, at its root, or slow enough for the linearised
 // step); otherwise F(x0), F'(x0) and f(x0) are left for the general part.
@@ -371,6 +419,36 @@ OOTS_HD bool integrate_prelude(const CellODE<Real> &C, Real x0, Real h, Real sig
                 return true;
             }
         }
+        // near the root: when one Newton step puts x_eq within both bending
+        // scales of x0, up to three Newton steps find it (f is smooth there)
+        // and the linearised solution about it finishes the cell
+        Real bm = Real(0);
+        for (int i = 0; i < NSMAX && i < C.ns; i++)
+            if (C.r[i].A > Real(0)) bm = m_max(bm, C.r[i].tab < 0 ? C.r[i].b : sigma0 * C.r[i].b);
+        const Real est = df0 < Real(0) ? m_abs(f0 / df0) : RealLimits<Real>::inf();
+        if (bm * est <= IntCfg<Real>::zlin() && est <= IntCfg<Real>::zlin() * (Real(1) - x0 + est)) {
+            Real xk = x0, fk = f0, Fk = F0, dfk = df0;
+            bool conv = false;
+            for (int it = 0; it < 3 && dfk < Real(0); it++) {
+                xk = m_min(m_max(xk - fk / dfk, Real(0)), Real(1));
+                Real dFk;
+                ode_F<Real, NSMAX>(C, xk, &Fk, &dFk);
+                fk = -Fk + C.c * (Real(1) - xk) * (Real(1) - xk);
+                dfk = -dFk - Real(2) * C.c * (Real(1) - xk);
+                if (m_abs(fk) <= Real(32) * RealLimits<Real>::eps() * (m_abs(Fk) + C.c * (Real(1) - xk) * (Real(1) - xk))) {
+                    conv = true;
+                    break;
+                }
+            }
+            if (conv) {
+                SrcEq<Real> Q[NSMAX];
+                Real Dinf, bmax;
+                root_slope<Real, NSMAX>(C, xk, sigma0, Q, Dinf, bmax);
+                if (near_root_solution<Real>(C, xk, x0 - xk, Dinf, bmax, h, R)) return true;
+                R.x = x0;          // not close enough: leave it to the general part
+                R.IR = Real(0);
+            }
+        }
     }
     return false;
 }
@@ -392,39 +470,10 @@ OOTS_HD IntResult<Real> integrate_general(const CellODE<Real> &C, Real x0, Real 
 
     // per-source values at the root and the slope at the root
     SrcEq<Real> Q[NSMAX];
-    Real bmax = Real(0);
-    Real Dinf = Real(2) * C.c * (Real(1) - xe);
-    for (int i = 0; i < NSMAX && i < C.ns; i++) {
-        const SrcRate<Real> &r = C.r[i];
-        Q[i].lne = -RealLimits<Real>::inf();
-        Q[i].Ne = Real(0);
-        if (!(r.A > Real(0))) continue;
-        if (r.tab < 0) {
-            Q[i].lne = -r.b * xe;
-            Dinf += r.A * r.b * m_exp(Q[i].lne);
-            bmax = m_max(bmax, r.b);
-        } else {
-            const DevTable<Real> &T = C.tabs[r.tab];
-            Q[i].Ne = r.Nin + r.b * xe;
-            Q[i].lne = m_log(r.p) + tab_dlnp(T, r.Nin, r.b * xe);
-            Real pe = m_exp(Q[i].lne);
-            if (pe > Real(0)) Dinf += -r.A * pe * r.b * tab_dlnp_dN(T, Q[i].Ne);
-            bmax = m_max(bmax, sigma0 * r.b);
-        }
-    }
-    Real ad0 = m_abs(d0);
-    // already next to the root (|d0| far below both bending scales): the
-    // linearised solution about x_eq, d(t) = d0 e^{-Dinf t}
-    if (bmax * ad0 <= IntCfg<Real>::zlin() && ad0 <= IntCfg<Real>::zlin() * (Real(1) - xe) && C.b0 == Real(0)) {
-        const Real e = m_exp(-Dinf * h);
-        R.x = xe + d0 * e;
-        const Real one = Real(1) - xe;
-        // int c (1 - xe - d)^2 dt = c one^2 h - 2 c one d0 (1 - e)/Dinf + c d0^2 (1 - e^2)/(2 Dinf)
-        const Real g1 = (Dinf * h > Real(1e-6)) ? -m_expm1(-Dinf * h) / Dinf : h;
-        const Real g2 = (Dinf * h > Real(1e-6)) ? -m_expm1(Real(-2) * Dinf * h) / (Real(2) * Dinf) : h;
-        R.IR = C.c * (one * one * h - Real(2) * one * d0 * g1 + d0 * d0 * g2);
-        return R;
-    }
+    Real Dinf, bmax;
+    root_slope<Real, NSMAX>(C, xe, sigma0, Q, Dinf, bmax);
+    const Real ad0 = m_abs(d0);
+    if (near_root_solution<Real>(C, xe, d0, Dinf, bmax, h, R)) return R;
     // start of the near-equilibrium tail in w = e^u: the secant slope bends on
     // |d| ~ 1/bmax (photoionisation) and |d| ~ 1 - xe (recombination)
     Real wt = Real(1);

@@ -45,7 +45,7 @@ def test_clumpy_adaptive_substeps_fp64(clumpy40, scheme):
         assert abs(dt_g / dt - 1.0) <= 1e-10, (k, dt_g, dt)
         c.step(dt_g)
         t = t_new
-        err = np.max(np.abs(c.get_neutral_fraction() - x.ravel()))
+        err = np.max(np.abs(c.get_neutral_fraction().ravel() - x.ravel()))
         assert err <= XTOL, (scheme, k, err)
 
 
@@ -70,7 +70,7 @@ def test_sixteen_sources_columns_dt_and_substeps_fp64(many_sources):
         assert abs(dt_g / dt - 1.0) <= 1e-10, (k, dt_g, dt)
         c.step(dt_g)
         t = t_new
-        err = np.max(np.abs(c.get_neutral_fraction() - x.ravel()))
+        err = np.max(np.abs(c.get_neutral_fraction().ravel() - x.ravel()))
         assert err <= XTOL, (k, err)
 
 
