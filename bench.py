@@ -143,7 +143,7 @@ def job_rate(units_per_rank, world, t_ms):
     return world * units_per_rank / (t_ms / 1e3)
 
 
-KERNEL_SOURCES = ("common.cuh", "integrator.cuh", "kernels.h", "oots_internal.h", "sweep.cu", "cell.cu")
+KERNEL_SOURCES = ("common.cuh", "integrator.cuh", "kernels.h", "oots_internal.h", "sweep_impl.cuh", "sweep_f.cu", "sweep_d.cu", "cell.cu")
 TRAFFIC_SUMMARY = os.path.join(ROOT, "profiles", "dram_traffic_lognormal128_mixed.md")
 
 

@@ -232,7 +232,7 @@ int oots_batch_destroy(oots_batch *b);
 
 /* ---- tuning and diagnostics ----------------------------------------------------------------- */
 
-/* Choose the sweep tile shape (0..5; -1 = automatic) -- the autotuner's hook. */
+/* Choose the sweep tile shape (0..6, see oots_tile_shape_info; -1 = automatic) -- the autotuner's hook. */
 int oots_set_tile_shape(oots_ctx *ctx, int shape);
 
 /* Number of tile shapes and the dimensions of one. */

@@ -174,10 +174,10 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
     }
 }
 
-// General pass: one warp per queued cell (HALF: queue 0, FULL: queue 1).
-// Warps take the next queued cell from a head counter (qcount[2 + queue]), so
-// the pass ends when the cells run out rather than when the warp that drew
-// the slowest share finishes.
+// General pass: one lane group per queued cell (a half warp in FP32, a warp
+// in FP64; HALF: queue 0, FULL: queue 1).  Groups take the next queued cell
+// from a head counter (qcount[2 + queue]), so the pass ends when the cells
+// run out rather than when the group that drew the slowest share finishes.
 // Every lane forms the same rates and runs the same root search; the
 // quadrature nodes are spread over the lanes (WarpEval).  Budget sums of FULL
 // are gathered per block in shared memory for up to eight grids and flushed
@@ -189,7 +189,10 @@ cell_general_kernel(const GridDev<Real> *grids, int ngrid, const long long *offs
 {
     __shared__ double s_ions[8], s_rec[8];
     __shared__ int s_gid[8];
-    const int lane = threadIdx.x & 31;
+    constexpr int W = GroupWidth<Real>::value;
+    const int lane32 = threadIdx.x & 31;
+    const int gbase = lane32 & ~(W - 1), lane = lane32 - gbase;
+    const unsigned gmask = W == 32 ? 0xffffffffu : (0xffffu << gbase);
     if (OP != OP_HALF) {
         if (threadIdx.x < 8) { s_ions[threadIdx.x] = 0.0; s_rec[threadIdx.x] = 0.0; s_gid[threadIdx.x] = -1; }
         __syncthreads();
@@ -199,7 +202,7 @@ cell_general_kernel(const GridDev<Real> *grids, int ngrid, const long long *offs
     for (;;) {
         unsigned q = 0;
         if (lane == 0) q = atomicAdd(&qcount[2 + qi], 1u);
-        q = __shfl_sync(0xffffffffu, q, 0);
+        q = __shfl_sync(gmask, q, gbase);
         if (q >= nq) break;
         const long long idx = queue[q];
         const int gi = find_grid(offsets, ngrid, idx);
@@ -224,7 +227,7 @@ cell_general_kernel(const GridDev<Real> *grids, int ngrid, const long long *offs
         IntResult<Real> R;
         Real F0, dF0, f0;
         if (!integrate_prelude<Real, NSMAX>(C, x0, h, G.sigma0, R, F0, dF0, f0))
-            R = integrate_general<Real, NSMAX>(C, x0, h, G.sigma0, R, F0, dF0, f0, WarpEval{lane});
+            R = integrate_general<Real, NSMAX>(C, x0, h, G.sigma0, R, F0, dF0, f0, GroupEval<W>{lane, gbase, gmask});
         if (lane == 0) {
             if (OP == OP_HALF) {
                 const_cast<Real *>(G.xh)[g] = R.x;

@@ -234,10 +234,11 @@ OOTS_HD Real newton_root(const CellODE<Real> &C, Real lo, Real hi, Real xk, Real
 //  - eval<N>(node, invD, dv): fills invD[l] = 1/D and dv[l] = d at the N
 //    quadrature nodes l = 0..N-1, where node(l, d) returns 1/D at node l and
 //    sets its deviation d.
-// The sequential form runs Newton from x0 and loops over the nodes.  The warp
-// form brackets the root with 32 samples at once and gives node l to lane l,
-// broadcasting the values: a whole warp integrates one cell, a panel costs one
-// evaluation of latency and the root search a scan plus a short polish.
+// The sequential form runs Newton from x0 and loops over the nodes.  The group
+// form (a half or whole warp per cell) brackets the root with one sample per
+// lane at once and gives node l to lane l, broadcasting the values: a panel
+// costs one evaluation of latency and the root search a scan plus a short
+// polish.
 struct SeqEval {
     static constexpr bool attenuation = true;    // A1's time-averaged attenuation when b0 > 0
     template <typename Real, int NSMAX>
@@ -254,9 +255,16 @@ struct SeqEval {
     }
 };
 #ifdef __CUDACC__
-struct WarpEval {
+template <int W> struct GroupEval {
+    static_assert(W == 16 || W == 32, "half warp or whole warp");
     static constexpr bool attenuation = false;   // integration passes only (b0 = 0)
-    int lane;
+    int lane;          // lane within the group, 0..W-1
+    int base;          // first lane of the group within its warp
+    unsigned mask;     // the group's lanes
+    template <typename Real> __device__ __forceinline__ Real bcast(Real v, int l) const
+    {
+        return __shfl_sync(mask, v, base + l);
+    }
     // Lane l samples f at a point of the bracket, ascending in x with l and
     // geometric towards the end the root lies away from (x for a root below
     // x0, 1 - x for a root above it) over nine decades; f > 0 exactly left
@@ -267,23 +275,22 @@ struct WarpEval {
     {
         const bool above = f0 > Real(0);                     // root in (x0, 1]
         const Real span = above ? Real(1) - x0 : x0;
-        // ratio e^-0.6476 per lane: 32 samples over nine decades of the span
-        const Real p = above ? Real(1) - span * m_exp(Real(-0.6476) * Real(lane + 1))
-                             : span * m_exp(Real(-0.6476) * Real(32 - lane));
+        const Real step = Real(-20.7233) / Real(W);          // ln(1e-9) over the group's samples
+        const Real p = above ? Real(1) - span * m_exp(step * Real(lane + 1)) : span * m_exp(step * Real(W - lane));
         Real Fp, dFp;
         ode_F<Real, NSMAX>(C, p, &Fp, &dFp);
         const Real fp = -Fp + C.c * (Real(1) - p) * (Real(1) - p);
         const Real dfp = -dFp - Real(2) * C.c * (Real(1) - p);
-        const unsigned pos = __ballot_sync(0xffffffffu, fp > Real(0));
-        const int j = (pos == 0xffffffffu) ? 32 : __ffs(~pos) - 1;   // first sample right of the root
+        const unsigned all = W == 32 ? 0xffffffffu : 0xffffu;
+        const unsigned pos = (__ballot_sync(mask, fp > Real(0)) >> base) & all;
+        const int j = (pos == all) ? W : __ffs(~pos) - 1;     // first sample right of the root
         // bracket [lo, hi] and the starting end
-        const Real pj = __shfl_sync(0xffffffffu, p, j & 31), pjm = __shfl_sync(0xffffffffu, p, (j + 31) & 31);
-        const Real fjm = __shfl_sync(0xffffffffu, fp, (j + 31) & 31), Fjm = __shfl_sync(0xffffffffu, Fp, (j + 31) & 31);
-        const Real dfjm = __shfl_sync(0xffffffffu, dfp, (j + 31) & 31);
-        const Real fj = __shfl_sync(0xffffffffu, fp, j & 31), Fj = __shfl_sync(0xffffffffu, Fp, j & 31);
-        const Real dfj = __shfl_sync(0xffffffffu, dfp, j & 31);
+        const int lj = j & (W - 1), ljm = (j + W - 1) & (W - 1);
+        const Real pj = bcast(p, lj), pjm = bcast(p, ljm);
+        const Real fjm = bcast(fp, ljm), Fjm = bcast(Fp, ljm), dfjm = bcast(dfp, ljm);
+        const Real fj = bcast(fp, lj), Fj = bcast(Fp, lj), dfj = bcast(dfp, lj);
         const Real lo = j > 0 ? pjm : (above ? x0 : Real(0));
-        const Real hi = j < 32 ? pj : (above ? Real(1) : x0);
+        const Real hi = j < W ? pj : (above ? Real(1) : x0);
         if (j > 0) return newton_root<Real, NSMAX>(C, lo, hi, pjm, fjm, Fjm, dfjm);
         if (above) return newton_root<Real, NSMAX>(C, lo, hi, x0, f0, F0, -dF0 - Real(2) * C.c * (Real(1) - x0));
         return newton_root<Real, NSMAX>(C, lo, hi, pj, fj, Fj, dfj);
@@ -291,16 +298,19 @@ struct WarpEval {
     template <int N, typename Real, typename Node>
     __device__ __forceinline__ void eval(const Node &node, Real *invD, Real *dv) const
     {
-        static_assert(N <= 32, "one node per lane");
+        static_assert(N <= W, "one node per lane");
         Real mi = Real(0), md = Real(0);
         if (lane < N) mi = node(lane, md);
 #pragma unroll
         for (int l = 0; l < N; l++) {
-            invD[l] = __shfl_sync(0xffffffffu, mi, l);
-            dv[l] = __shfl_sync(0xffffffffu, md, l);
+            invD[l] = bcast(mi, l);
+            dv[l] = bcast(md, l);
         }
     }
 };
+// lanes per cell of the general pass: the FP32 panel's 3G = 12 nodes fit a
+// half warp (two cells per warp); FP64's 24 take a whole warp
+template <typename Real> struct GroupWidth { enum { value = 3 * IntCfg<Real>::G <= 16 ? 16 : 32 }; };
 #endif
 
 // Per-source values at the root x_eq and the slope there: Dinf = -f'(x_eq),

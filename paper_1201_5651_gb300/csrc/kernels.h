@@ -10,16 +10,18 @@ struct ff;
 template <typename Real> struct ColT;
 
 // Tile shapes of the wavefront sweep: (id, TX, TY, TZ); one chain thread per
-// (j,k) column (TY*TZ a multiple of 32) plus one producer warp.
+// (j,k) column (TY*TZ a multiple of 32) plus one producer warp.  Shapes with
+// TY*TZ = 32 keep the whole plane chain in one warp.
 #define OOTS_SHAPES(X) \
     X(0, 16, 8, 8)     \
-    X(1, 32, 8, 8)     \
+    X(1, 16, 8, 4)     \
     X(2, 16, 16, 16)   \
-    X(3, 8, 16, 16)    \
+    X(3, 32, 8, 4)     \
     X(4, 8, 8, 8)      \
-    X(5, 16, 16, 8)
-enum { NUM_SHAPES = 6 };
-static const int SHAPE_DIMS[NUM_SHAPES][3] = {{16, 8, 8}, {32, 8, 8}, {16, 16, 16}, {8, 16, 16}, {8, 8, 8}, {16, 16, 8}};
+    X(5, 16, 16, 8)    \
+    X(6, 8, 8, 4)
+enum { NUM_SHAPES = 7 };
+static const int SHAPE_DIMS[NUM_SHAPES][3] = {{16, 8, 8}, {16, 8, 4}, {16, 16, 16}, {32, 8, 4}, {8, 8, 8}, {16, 16, 8}, {8, 8, 4}};
 
 template <typename Real> struct SweepParams {
     const GridDev<Real> *grids;

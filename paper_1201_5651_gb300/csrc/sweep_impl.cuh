@@ -31,6 +31,7 @@
 // halo-adjacent cells once their chunk's halo is staged), so a plane costs
 // one weighted difference sum and one column add.  Shared-memory rows are
 // padded so that a plane's cells sit in distinct banks.
+#pragma once
 #include "common.cuh"
 #include "integrator.cuh"
 #include "kernels.h"
@@ -51,10 +52,12 @@ __device__ __forceinline__ unsigned long long tagged(unsigned bits, unsigned epo
 {
     return ((unsigned long long)epoch << 32) | bits;
 }
-// barrier among the chain warps only (the producer warp does not take part)
+// barrier among the chain warps only (the producer warp does not take part);
+// a one-warp chain needs only the warp barrier
 template <int N> __device__ __forceinline__ void chain_sync()
 {
-    asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
+    if (N == 32) __syncwarp();
+    else asm volatile("bar.sync 1, %0;" ::"n"(N) : "memory");
 }
 // Chunk hand-off from the producer warp to the chain warps: named barrier
 // 2 + k % 14 for chunk k, N = chain threads + 32.  The producer arrives
@@ -709,8 +712,6 @@ bool sweep_shape_ok(int shape)
 #undef OOTS_SM
     return sm > 0 && (int)sm <= max_optin_smem();
 }
-template bool sweep_shape_ok<double>(int);
-template bool sweep_shape_ok<float>(int);
 
 template <typename Real>
 int sweep_occupancy(int shape, int mode)
@@ -758,11 +759,5 @@ cudaError_t prepare_sweeps()
     return e;
 }
 
-template int sweep_occupancy<double>(int, int);
-template int sweep_occupancy<float>(int, int);
-template cudaError_t prepare_sweeps<double>();
-template cudaError_t prepare_sweeps<float>();
-template cudaError_t launch_sweep<double>(const SweepParams<double> &, int, int, int, cudaStream_t);
-template cudaError_t launch_sweep<float>(const SweepParams<float> &, int, int, int, cudaStream_t);
 
 } // namespace oots
