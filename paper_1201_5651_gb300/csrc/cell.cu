@@ -17,6 +17,9 @@
 
 namespace oots {
 
+// general-pass queue record of a single-source cell: x0, n, A, b, N_in, p, F(x0), F'(x0), f(x0)
+constexpr int QREC = 9;
+
 __device__ __forceinline__ int find_grid(const long long *off, int ngrid, long long idx)
 {
     int lo = 0, hi = ngrid - 1;
@@ -73,7 +76,7 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 template <typename Real, int OP, int NSMAX>
 __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, int ngrid, const long long *offsets,
                                                    long long total, const DevTable<Real> *tabs, unsigned *queue,
-                                                   unsigned *qcount)
+                                                   unsigned *qcount, Real *qrec)
 {
     __shared__ double sh[32];
     __shared__ int s_grid_lo, s_grid_hi;
@@ -97,6 +100,7 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
         double dtmin = __longlong_as_double(0x7ff0000000000000ll);
         double ions = 0.0, rec = 0.0;
         bool defer = false;
+        Real rv[QREC];
         if (active) {
             const long long g = idx - offsets[gi];
             const int X = (int)(g % G.nx);
@@ -136,6 +140,11 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
                     }
                 } else {
                     defer = true;
+                    if (NSMAX == 1) {
+                        // what the general pass would otherwise recompute
+                        rv[0] = x0; rv[1] = n; rv[2] = r[0].A; rv[3] = r[0].b; rv[4] = r[0].Nin; rv[5] = r[0].p;
+                        rv[6] = F0; rv[7] = dF0; rv[8] = f0;
+                    }
                 }
             }
         }
@@ -147,7 +156,13 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
                 unsigned base = 0;
                 if (lane == leader) base = atomicAdd(qcount + (OP == OP_HALF ? 0 : 1), (unsigned)__popc(m));
                 base = __shfl_sync(0xffffffffu, base, leader);
-                if (defer) queue[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)idx;
+                if (defer) {
+                    const unsigned slot = base + __popc(m & ((1u << lane) - 1u));
+                    queue[slot] = (unsigned)idx;
+                    if (NSMAX == 1)
+#pragma unroll
+                        for (int v = 0; v < QREC; v++) qrec[(size_t)slot * QREC + v] = rv[v];
+                }
             }
         }
         if (OP == OP_RATEDT) {
@@ -185,7 +200,7 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
 template <typename Real, int OP, int NSMAX>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2)
 cell_general_kernel(const GridDev<Real> *grids, int ngrid, const long long *offsets, const DevTable<Real> *tabs,
-                    const unsigned *queue, unsigned *qcount)
+                    const unsigned *queue, unsigned *qcount, const Real *qrec)
 {
     __shared__ double s_ions[8], s_rec[8];
     __shared__ int s_gid[8];
@@ -210,23 +225,35 @@ cell_general_kernel(const GridDev<Real> *grids, int ngrid, const long long *offs
         DevState *st = G.st;
         const double dtd = st->dt;
         const long long g = idx - offsets[gi];
-        const int X = (int)(g % G.nx);
-        const int Y = (int)((g / G.nx) % G.ny);
-        const int Z = (int)(g / ((long long)G.nx * G.ny));
-        const Real n = G.n ? G.n[g] : G.n_uniform;
-        const Real x0 = G.x[g];
         SrcRate<Real> r[NSMAX];
-        const Real *Ncol = (OP == OP_FULL2) ? G.N2 : G.N1;
         CellODE<Real> C;
-        C.ns = cell_rates<Real, NSMAX>(G, Ncol, tabs, X, Y, Z, g, n, r);
+        Real n, x0, F0, dF0, f0;
+        IntResult<Real> R;
+        const Real h = Real(OP == OP_HALF ? 0.5 * dtd : dtd);
+        bool done = false;
+        if (NSMAX == 1) {
+            // one source: the closed-form pass left its rates and f(x0)
+            const Real *rv = qrec + (size_t)q * QREC;
+            x0 = rv[0]; n = rv[1];
+            r[0].A = rv[2]; r[0].b = rv[3]; r[0].Nin = rv[4]; r[0].p = rv[5]; r[0].tab = G.tab[0];
+            F0 = rv[6]; dF0 = rv[7]; f0 = rv[8];
+            C.ns = 1;
+            R.x = x0; R.IR = Real(0); R.lnfav = Real(0);
+        } else {
+            const int X = (int)(g % G.nx);
+            const int Y = (int)((g / G.nx) % G.ny);
+            const int Z = (int)(g / ((long long)G.nx * G.ny));
+            n = G.n ? G.n[g] : G.n_uniform;
+            x0 = G.x[g];
+            const Real *Ncol = (OP == OP_FULL2) ? G.N2 : G.N1;
+            C.ns = cell_rates<Real, NSMAX>(G, Ncol, tabs, X, Y, Z, g, n, r);
+        }
         C.c = G.alpha * n;
         C.b0 = Real(0);
         C.r = r;
         C.tabs = tabs;
-        const Real h = Real(OP == OP_HALF ? 0.5 * dtd : dtd);
-        IntResult<Real> R;
-        Real F0, dF0, f0;
-        if (!integrate_prelude<Real, NSMAX>(C, x0, h, G.sigma0, R, F0, dF0, f0))
+        if (NSMAX != 1) done = integrate_prelude<Real, NSMAX>(C, x0, h, G.sigma0, R, F0, dF0, f0);
+        if (!done)
             R = integrate_general<Real, NSMAX>(C, x0, h, G.sigma0, R, F0, dF0, f0, GroupEval<W>{lane, gbase, gmask});
         if (lane == 0) {
             if (OP == OP_HALF) {
@@ -295,18 +322,18 @@ __global__ void finalize_kernel(const GridDev<Real> *grids, int ngrid, int stage
 template <typename Real, int NSMAX>
 static cudaError_t launch_cell_ns(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
                                   const DevTable<Real> *tabs, int op, unsigned *queue, unsigned *qcount,
-                                  int gen_blocks, cudaStream_t s)
+                                  Real *qrec, int gen_blocks, cudaStream_t s)
 {
     const int bs = 256;
     const long long nb = (total + bs - 1) / bs;
     switch (op) {
-    case OP_RATEDT: cell_kernel<Real, OP_RATEDT, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount); break;
-    case OP_HALF: cell_kernel<Real, OP_HALF, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount); break;
-    case OP_FULL1: cell_kernel<Real, OP_FULL1, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount); break;
-    case OP_FULL2: cell_kernel<Real, OP_FULL2, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount); break;
-    case OP_HALF | OP_GENERAL: cell_general_kernel<Real, OP_HALF, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
-    case OP_FULL1 | OP_GENERAL: cell_general_kernel<Real, OP_FULL1, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
-    case OP_FULL2 | OP_GENERAL: cell_general_kernel<Real, OP_FULL2, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
+    case OP_RATEDT: cell_kernel<Real, OP_RATEDT, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec); break;
+    case OP_HALF: cell_kernel<Real, OP_HALF, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec); break;
+    case OP_FULL1: cell_kernel<Real, OP_FULL1, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec); break;
+    case OP_FULL2: cell_kernel<Real, OP_FULL2, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec); break;
+    case OP_HALF | OP_GENERAL: cell_general_kernel<Real, OP_HALF, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount, qrec); break;
+    case OP_FULL1 | OP_GENERAL: cell_general_kernel<Real, OP_FULL1, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount, qrec); break;
+    case OP_FULL2 | OP_GENERAL: cell_general_kernel<Real, OP_FULL2, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount, qrec); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -317,12 +344,14 @@ static cudaError_t launch_cell_ns(const GridDev<Real> *grids, int ngrid, const l
 template <typename Real>
 cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
                         const DevTable<Real> *tabs, int op, int nsmax, unsigned *queue, unsigned *qcount,
-                        int gen_blocks, cudaStream_t s)
+                        Real *qrec, int gen_blocks, cudaStream_t s)
 {
     if (total <= 0) return cudaSuccess;
-    if (nsmax <= 1) return launch_cell_ns<Real, 1>(grids, ngrid, offsets, total, tabs, op, queue, qcount, gen_blocks, s);
-    return launch_cell_ns<Real, MAX_SRC>(grids, ngrid, offsets, total, tabs, op, queue, qcount, gen_blocks, s);
+    if (nsmax <= 1) return launch_cell_ns<Real, 1>(grids, ngrid, offsets, total, tabs, op, queue, qcount, qrec, gen_blocks, s);
+    return launch_cell_ns<Real, MAX_SRC>(grids, ngrid, offsets, total, tabs, op, queue, qcount, nullptr, gen_blocks, s);
 }
+
+template <typename Real> size_t queue_record_bytes() { return QREC * sizeof(Real); }
 
 // Resident 256-thread blocks of the general pass per SM.
 template <typename Real>
@@ -343,9 +372,13 @@ cudaError_t launch_finalize(const GridDev<Real> *grids, int ngrid, int stage, un
 }
 
 template cudaError_t launch_cell<double>(const GridDev<double> *, int, const long long *, long long,
-                                         const DevTable<double> *, int, int, unsigned *, unsigned *, int, cudaStream_t);
+                                         const DevTable<double> *, int, int, unsigned *, unsigned *, double *, int,
+                                         cudaStream_t);
 template cudaError_t launch_cell<float>(const GridDev<float> *, int, const long long *, long long,
-                                        const DevTable<float> *, int, int, unsigned *, unsigned *, int, cudaStream_t);
+                                        const DevTable<float> *, int, int, unsigned *, unsigned *, float *, int,
+                                        cudaStream_t);
+template size_t queue_record_bytes<double>();
+template size_t queue_record_bytes<float>();
 template int cell_general_occupancy<double>(int);
 template int cell_general_occupancy<float>(int);
 template cudaError_t launch_finalize<double>(const GridDev<double> *, int, int, unsigned *, cudaStream_t);

@@ -136,6 +136,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     long long *d_offsets = nullptr;
     long long total = 0;
     unsigned *d_queue = nullptr;       // cells left to the general pass (one entry per cell at most)
+    Real *d_qrec = nullptr;            // their closed-form results (single-source launch sets)
     unsigned *d_qcount = nullptr;      // queue lengths of the half and full integrations
     int gen_blocks = 1;                // grid of the general pass
     int nblocks0 = 1, nblocks1 = 1;
@@ -160,6 +161,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         for (void *p : tabmem) cudaFree(p);
         cudaFree(d_offsets);
         cudaFree(d_queue);
+        cudaFree(d_qrec);
         cudaFree(d_qcount);
     }
 
@@ -296,6 +298,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         CU(cudaMemcpy(d_offsets, offs.data(), offs.size() * sizeof(long long), cudaMemcpyHostToDevice));
         if (total > 0xffffffffll) return fail(OOTS_E_INVAL, "%lld cells in one call (the queue holds 32-bit indices)", total);
         CU(cudaMalloc(&d_queue, (size_t)std::max(total, 1ll) * sizeof(unsigned)));
+        if (nsmax <= 1) CU(cudaMalloc(&d_qrec, (size_t)std::max(total, 1ll) * queue_record_bytes<Real>()));
         CU(cudaMalloc(&d_qcount, 8 * sizeof(unsigned)));
         CU(cudaMemset(d_qcount, 0, 8 * sizeof(unsigned)));
         if (!jobs.empty()) {
@@ -355,13 +358,14 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     int cell(cudaStream_t s, int op)
     {
         if (prof) prof->mark(0);
-        CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op, nsmax, d_queue, d_qcount, gen_blocks, s));
+        CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op, nsmax, d_queue, d_qcount, d_qrec,
+                             gen_blocks, s));
         if (prof) prof->mark(op == OP_RATEDT ? OOTS_K_RATEDT : (op == OP_HALF ? OOTS_K_HALF : OOTS_K_FULL));
         if (op == OP_RATEDT) return OOTS_OK;
         // the cells no closed form settles, one warp each
         if (prof) prof->mark(0);
         CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op | OP_GENERAL, nsmax, d_queue,
-                             d_qcount, gen_blocks, s));
+                             d_qcount, d_qrec, gen_blocks, s));
         if (prof) prof->mark(op == OP_HALF ? OOTS_K_HALF_GENERAL : OOTS_K_FULL_GENERAL);
         return OOTS_OK;
     }
