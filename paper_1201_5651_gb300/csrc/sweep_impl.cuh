@@ -23,10 +23,12 @@
 // fence or acquire is needed.  The epoch advances once per launch (the last
 // CTA to finish stores it), so words left by earlier launches never match.
 //
-// Each CTA holds the chain warps and one producer warp.  The producer stages
-// each chunk's halo cells (a compile-time list sorted by the first plane that
-// reads them) from the upstream faces into shared memory, with bounded
-// polling, running ahead of the chain.  The chain warps form each cell's normalised neighbour
+// Each CTA holds the chain warps, one producer warp and one writer warp.  The
+// producer stages each chunk's halo cells (a compile-time list sorted by the
+// first plane that reads them) from the upstream faces into shared memory,
+// with bounded polling, running ahead of the chain.  The writer publishes the
+// tile's downstream face cells chunk by chunk as the chain completes them, so
+// the chain's plane step holds no global stores.  The chain warps form each cell's normalised neighbour
 // weights off the critical path (interior cells before the first wait,
 // halo-adjacent cells once their chunk's halo is staged), so a plane costs
 // one weighted difference sum and one column add.  Shared-memory rows are
@@ -214,8 +216,58 @@ constexpr HaloList<TX, TY, TZ> make_halo_list()
 template <int TX, int TY, int TZ>
 __device__ const HaloList<TX, TY, TZ> g_halo_list = make_halo_list<TX, TY, TZ>();
 
+// The tile's own downstream face cells (li = TX-1, lj = TY-1, lk = TZ-1) sorted
+// by the plane that completes them, packed like the halo list (halo index,
+// index within the face, face); a cell on two or three faces appears once per
+// face.  The writer warp publishes them chunk by chunk.
+template <int TX, int TY, int TZ> struct FaceList {
+    enum { N = TY * TZ + TX * TZ + TX * TY };
+    unsigned e[N];
+    unsigned short start[TileLayout<TX, TY, TZ>::NP + 1];
+};
+template <int TX, int TY, int TZ>
+constexpr void face_entry(int q, int &key, unsigned &packed)
+{
+    typedef TileLayout<TX, TY, TZ> L;
+    int li = 0, lj = 0, lk = 0, face = 0, fq = 0;
+    if (q < TY * TZ) {
+        lj = q % TY; lk = q / TY; li = TX - 1; face = 0; fq = lk * TY + lj;
+    } else if (q < TY * TZ + TX * TZ) {
+        const int r = q - TY * TZ;
+        li = r % TX; lk = r / TX; lj = TY - 1; face = 1; fq = lk * TX + li;
+    } else {
+        const int r = q - TY * TZ - TX * TZ;
+        li = r % TX; lj = r / TX; lk = TZ - 1; face = 2; fq = lj * TX + li;
+    }
+    key = li + lj + lk;
+    packed = (unsigned)L::h(li, lj, lk) | ((unsigned)fq << 14) | ((unsigned)face << 26);
+}
+template <int TX, int TY, int TZ>
+constexpr FaceList<TX, TY, TZ> make_face_list()
+{
+    typedef TileLayout<TX, TY, TZ> L;
+    typedef FaceList<TX, TY, TZ> FL;
+    FL F{};
+    int cnt[L::NP + 1] = {};
+    for (int q = 0; q < FL::N; q++) {
+        int key = 0; unsigned p = 0;
+        face_entry<TX, TY, TZ>(q, key, p);
+        cnt[key + 1]++;
+    }
+    for (int k = 0; k < L::NP; k++) cnt[k + 1] += cnt[k];
+    for (int k = 0; k <= L::NP; k++) F.start[k] = (unsigned short)cnt[k];
+    for (int q = 0; q < FL::N; q++) {
+        int key = 0; unsigned p = 0;
+        face_entry<TX, TY, TZ>(q, key, p);
+        F.e[cnt[key]++] = p;
+    }
+    return F;
+}
+template <int TX, int TY, int TZ>
+__device__ const FaceList<TX, TY, TZ> g_face_list = make_face_list<TX, TY, TZ>();
+
 template <typename Real, int TX, int TY, int TZ, int MODE>
-__global__ void __launch_bounds__(TY *TZ + 32)
+__global__ void __launch_bounds__(TY *TZ + 64)
 sweep_kernel(SweepParams<Real> P)
 {
     typedef typename ColT<Real>::type Col;
@@ -236,8 +288,10 @@ sweep_kernel(SweepParams<Real> P)
     Real *sQ = sDI + HSZ;                              // 3 x HSZ neighbour weights (see below)
     unsigned char *sMode = reinterpret_cast<unsigned char *>(sQ + 3 * HSZ); // chain mode (see below)
     __shared__ unsigned s_ticket;
+    __shared__ volatile int s_done;              // chunks the chain has completed (for the writer)
     __shared__ double s_bud[3];
     const HaloList<TX, TY, TZ> &HL = g_halo_list<TX, TY, TZ>;
+    const FaceList<TX, TY, TZ> &FL = g_face_list<TX, TY, TZ>;
 
     typedef FaceWords<Real> FW;
     unsigned long long *const faces = P.faces;
@@ -290,6 +344,7 @@ sweep_kernel(SweepParams<Real> P)
             // tiles skip, so no wait is left pending)
             if (t < (unsigned)P.nitems && P.grids[P.jobs[P.items[t].job].grid].st->done) t |= 0x80000000u;
             s_ticket = t;
+            s_done = 0;
         }
         __syncthreads();
         const unsigned tk = s_ticket;
@@ -304,7 +359,31 @@ sweep_kernel(SweepParams<Real> P)
         const Real *xin = (P.which == 1) ? G.xh : G.x;
         const Real dx = G.dx, sig = G.sigma0, tau0 = G.tau0;
 
-        if (tid >= NT) {
+        if (tid >= NT + 32) {
+            // ---------------- writer warp ----------------
+            // after chunk k, the face cells its planes completed go out as tagged
+            // words (the chain's barrier and the shared counter order the chain's
+            // shared-memory writes before these reads)
+            const int lane = tid - NT - 32;
+            if (tile_self != P.skip_publish) {
+                unsigned long long *const fbase = faces + tile_self * 3 * FMAX * FW::W;
+                int k = 0;
+                for (int m0 = 0; m0 < NP; m0 += chunk, k++) {
+                    const int m1 = min(m0 + chunk, NP);
+                    long long spins = 0;
+                    while (s_done <= k) {
+                        if (++spins > (P.spin_limit << 4)) { atomicCAS(P.err, 0, (int)DEVERR_TIMEOUT); break; }
+                        __nanosleep(32);
+                    }
+                    __threadfence_block();
+                    for (int q = FL.start[m0] + lane; q < FL.start[m1]; q += 32) {
+                        const unsigned en = __ldg(&FL.e[q]);
+                        const int h = en & 0x3fffu;
+                        FW::store(fbase + (((en >> 26) & 3u) * FMAX + ((en >> 14) & 0xfffu)) * FW::W, sN[h], sW[h], epoch);
+                    }
+                }
+            }
+        } else if (tid >= NT) {
             // ---------------- producer warp ----------------
             const int lane = tid - NT;
             // zero the halo (read as absent until staged)
@@ -437,8 +516,7 @@ sweep_kernel(SweepParams<Real> P)
                 }
             }
 
-            unsigned long long *const fbase = faces + tile_self * 3 * FMAX * FW::W;
-            const bool publish = tile_self != P.skip_publish;
+
             int k = 0;
             for (int m0 = 0; m0 < NP; m0 += chunk, k++) {
                 const int m1 = min(m0 + chunk, NP);
@@ -621,15 +699,11 @@ sweep_kernel(SweepParams<Real> P)
                             }
                             sN[h] = Nout;
                         }
-                        // downstream faces are published as their cells complete
-                        if (publish) {
-                            if (li == TX - 1) FW::store(fbase + (0 * FMAX + lk * TY + lj) * FW::W, Nout, wout, epoch);
-                            if (lj == TY - 1) FW::store(fbase + (1 * FMAX + lk * TX + li) * FW::W, Nout, wout, epoch);
-                            if (lk == TZ - 1) FW::store(fbase + (2 * FMAX + lj * TX + li) * FW::W, Nout, wout, epoch);
-                        }
                     }
                     chain_sync<NT>();
                 }
+                // 3. chunk done: its face cells go to the writer warp
+                if (tid == 0) { __threadfence_block(); s_done = k + 1; }
             }
 
             // 4. entry columns of the tile's cells
@@ -682,7 +756,7 @@ template <typename Real, int TX, int TY, int TZ, int MODE>
 static cudaError_t launch_shape(const SweepParams<Real> &P, int nblocks, cudaStream_t s)
 {
     constexpr size_t sm = sweep_smem<Real, TX, TY, TZ>();
-    sweep_kernel<Real, TX, TY, TZ, MODE><<<nblocks, TY * TZ + 32, sm, s>>>(P);
+    sweep_kernel<Real, TX, TY, TZ, MODE><<<nblocks, TY * TZ + 64, sm, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -721,8 +795,8 @@ int sweep_occupancy(int shape, int mode)
 #define OOTS_OCC(ID, TX, TY, TZ)                                                                      \
     if (shape == ID) {                                                                                \
         constexpr size_t sm = sweep_smem<Real, TX, TY, TZ>();                                         \
-        if (mode == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 0>, TY * TZ + 32, sm); \
-        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 1>, TY * TZ + 32, sm); \
+        if (mode == 0) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 0>, TY * TZ + 64, sm); \
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_kernel<Real, TX, TY, TZ, 1>, TY * TZ + 64, sm); \
     }
     OOTS_SHAPES(OOTS_OCC)
 #undef OOTS_OCC
