@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -74,7 +75,7 @@ class Clocks:
         self.proc = None
         self.skip = 0
         self.index = index
-        self.out = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.out = os.environ.get("OOTS_CLOCKS_LOG") or os.path.join(tempfile.gettempdir(), f"oots_clocks_rank{index}.csv")
 
     def start(self):
         try:

@@ -31,9 +31,11 @@ __device__ __forceinline__ int find_grid(const long long *off, int ngrid, long l
 }
 
 // Rate parameters of every source for the cell at global index g = (X,Y,Z).
+// with_p = false leaves r[s].p of tabulated sources to the caller.
 template <typename Real, int NSMAX>
 __device__ __forceinline__ int cell_rates(const GridDev<Real> &G, const Real *Ncol, const DevTable<Real> *tabs,
-                                          int X, int Y, int Z, long long g, Real n, SrcRate<Real> *r)
+                                          int X, int Y, int Z, long long g, Real n, SrcRate<Real> *r,
+                                          bool with_p = true)
 {
     for (int s = 0; s < NSMAX && s < G.nsrc; s++) {
         const int i = X >= G.vtx[s][0] ? X - G.vtx[s][0] : G.vtx[s][0] - 1 - X;
@@ -53,30 +55,33 @@ __device__ __forceinline__ int cell_rates(const GridDev<Real> &G, const Real *Nc
         } else {
             r[s].A = G.qfac[s] / (n * r2 * sf);
             r[s].b = n * G.dx * sf;
-            r[s].p = m_exp(tab_lnp(tabs[r[s].tab], N));
+            if (with_p) r[s].p = m_exp(tab_lnp(tabs[r[s].tab], N));
         }
     }
     return G.nsrc;
 }
 
-template <typename Real>
-__device__ __forceinline__ double block_sum(double v, double *sh)
+// Block sums of two values in one pass (one pair of barriers); thread 0 gets both.
+__device__ __forceinline__ void block_sum2(double &a, double &b, double *sh)
 {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     __syncthreads();
-    if (lane == 0) sh[wid] = v;
+    if (lane == 0) { sh[2 * wid] = a; sh[2 * wid + 1] = b; }
     __syncthreads();
-    double s = 0.0;
-    if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += sh[w];
-    return s;
+    if (threadIdx.x == 0) {
+        a = 0.0; b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) { a += sh[2 * w]; b += sh[2 * w + 1]; }
+    }
 }
 
 template <typename Real, int OP, int NSMAX>
 __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, int ngrid, const long long *offsets,
                                                    long long total, const DevTable<Real> *tabs, unsigned *queue,
-                                                   unsigned *qcount, Real *qrec)
+                                                   unsigned *qcount, Real *qrec, Real *rcache, int use_cache)
 {
     __shared__ double sh[32];
     __shared__ int s_grid_lo, s_grid_hi;
@@ -111,14 +116,25 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
             SrcRate<Real> r[NSMAX];
             const Real *Ncol = (OP == OP_FULL2) ? G.N2 : G.N1;
             CellODE<Real> C;
-            C.ns = cell_rates<Real, NSMAX>(G, Ncol, tabs, X, Y, Z, g, n, r);
+            // single source, same state and columns as this substep's dt pass:
+            // its transmitted fraction and F, F' at x0 come from the rate cache
+            const bool cached = NSMAX == 1 && (OP == OP_HALF || OP == OP_FULL1) && use_cache;
+            C.ns = cell_rates<Real, NSMAX>(G, Ncol, tabs, X, Y, Z, g, n, r, !cached);
+            if (cached && C.ns > 0) r[0].p = rcache[idx];
             C.c = G.alpha * n;
             C.b0 = Real(0);
             C.r = r;
             C.tabs = tabs;
             if (OP == OP_RATEDT) {
                 // Eq. 4 with T fixed: K1 t_rec, K3 max(0.05, x)/|dx/dt|, K4/|dx/dt|
-                const double xd = fabs((double)ode_rhs<Real, NSMAX>(C, x0));
+                Real F, dF;
+                ode_F<Real, NSMAX>(C, x0, &F, &dF);
+                const double xd = fabs((double)(-F + C.c * (Real(1) - x0) * (Real(1) - x0)));
+                if (NSMAX == 1 && rcache && C.ns > 0) {
+                    rcache[idx] = r[0].p;
+                    rcache[total + idx] = F;
+                    rcache[2 * total + idx] = dF;
+                }
                 if (st->K1 > 0) dtmin = fmin(dtmin, st->K1 / (double(G.alpha) * double(n)));
                 if (xd > 0) {
                     if (st->K3 > 0) dtmin = fmin(dtmin, st->K3 * fmax(0.05, (double)x0) / xd);
@@ -127,9 +143,10 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
             } else {
                 // closed forms here; the rest goes to the warp-per-cell pass
                 IntResult<Real> R;
-                Real F0, dF0, f0;
+                Real F0 = Real(0), dF0 = Real(0), f0;
                 const Real h = Real(OP == OP_HALF ? 0.5 * dtd : dtd);
-                if (integrate_prelude<Real, NSMAX>(C, x0, h, G.sigma0, R, F0, dF0, f0)) {
+                if (cached && C.ns > 0) { F0 = rcache[total + idx]; dF0 = rcache[2 * total + idx]; }
+                if (integrate_prelude<Real, NSMAX>(C, x0, h, G.sigma0, R, F0, dF0, f0, cached && C.ns > 0)) {
                     if (OP == OP_HALF) {
                         const_cast<Real *>(G.xh)[g] = R.x;
                     } else {
@@ -177,8 +194,8 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
                 if (m < 1e300) atomicMin(&st->dt_bits, (unsigned long long)__double_as_longlong(m));
             }
         } else if (OP == OP_FULL1 || OP == OP_FULL2) {
-            const double si = block_sum<Real>(ions, sh);
-            const double sr = block_sum<Real>(rec, sh);
+            double si = ions, sr = rec;
+            block_sum2(si, sr, sh);
             if (threadIdx.x == 0 && (si != 0.0 || sr != 0.0)) {
                 atomicAdd(&st->bud_step[1], si + sr);   // absorbed = new ions + recombinations
                 atomicAdd(&st->bud_step[2], si);
@@ -322,15 +339,15 @@ __global__ void finalize_kernel(const GridDev<Real> *grids, int ngrid, int stage
 template <typename Real, int NSMAX>
 static cudaError_t launch_cell_ns(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
                                   const DevTable<Real> *tabs, int op, unsigned *queue, unsigned *qcount,
-                                  Real *qrec, int gen_blocks, cudaStream_t s)
+                                  Real *qrec, Real *rcache, int use_cache, int gen_blocks, cudaStream_t s)
 {
     const int bs = 256;
     const long long nb = (total + bs - 1) / bs;
     switch (op) {
-    case OP_RATEDT: cell_kernel<Real, OP_RATEDT, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec); break;
-    case OP_HALF: cell_kernel<Real, OP_HALF, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec); break;
-    case OP_FULL1: cell_kernel<Real, OP_FULL1, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec); break;
-    case OP_FULL2: cell_kernel<Real, OP_FULL2, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec); break;
+    case OP_RATEDT: cell_kernel<Real, OP_RATEDT, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec, rcache, use_cache); break;
+    case OP_HALF: cell_kernel<Real, OP_HALF, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec, rcache, use_cache); break;
+    case OP_FULL1: cell_kernel<Real, OP_FULL1, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec, rcache, use_cache); break;
+    case OP_FULL2: cell_kernel<Real, OP_FULL2, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec, rcache, use_cache); break;
     case OP_HALF | OP_GENERAL: cell_general_kernel<Real, OP_HALF, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount, qrec); break;
     case OP_FULL1 | OP_GENERAL: cell_general_kernel<Real, OP_FULL1, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount, qrec); break;
     case OP_FULL2 | OP_GENERAL: cell_general_kernel<Real, OP_FULL2, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount, qrec); break;
@@ -344,11 +361,14 @@ static cudaError_t launch_cell_ns(const GridDev<Real> *grids, int ngrid, const l
 template <typename Real>
 cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
                         const DevTable<Real> *tabs, int op, int nsmax, unsigned *queue, unsigned *qcount,
-                        Real *qrec, int gen_blocks, cudaStream_t s)
+                        Real *qrec, Real *rcache, int use_cache, int gen_blocks, cudaStream_t s)
 {
     if (total <= 0) return cudaSuccess;
-    if (nsmax <= 1) return launch_cell_ns<Real, 1>(grids, ngrid, offsets, total, tabs, op, queue, qcount, qrec, gen_blocks, s);
-    return launch_cell_ns<Real, MAX_SRC>(grids, ngrid, offsets, total, tabs, op, queue, qcount, nullptr, gen_blocks, s);
+    if (nsmax <= 1)
+        return launch_cell_ns<Real, 1>(grids, ngrid, offsets, total, tabs, op, queue, qcount, qrec, rcache,
+                                       use_cache && rcache, gen_blocks, s);
+    return launch_cell_ns<Real, MAX_SRC>(grids, ngrid, offsets, total, tabs, op, queue, qcount, nullptr, nullptr, 0,
+                                         gen_blocks, s);
 }
 
 template <typename Real> size_t queue_record_bytes() { return QREC * sizeof(Real); }
@@ -372,11 +392,11 @@ cudaError_t launch_finalize(const GridDev<Real> *grids, int ngrid, int stage, un
 }
 
 template cudaError_t launch_cell<double>(const GridDev<double> *, int, const long long *, long long,
-                                         const DevTable<double> *, int, int, unsigned *, unsigned *, double *, int,
-                                         cudaStream_t);
+                                         const DevTable<double> *, int, int, unsigned *, unsigned *, double *, double *,
+                                         int, int, cudaStream_t);
 template cudaError_t launch_cell<float>(const GridDev<float> *, int, const long long *, long long,
-                                        const DevTable<float> *, int, int, unsigned *, unsigned *, float *, int,
-                                        cudaStream_t);
+                                        const DevTable<float> *, int, int, unsigned *, unsigned *, float *, float *, int,
+                                        int, cudaStream_t);
 template size_t queue_record_bytes<double>();
 template size_t queue_record_bytes<float>();
 template int cell_general_occupancy<double>(int);

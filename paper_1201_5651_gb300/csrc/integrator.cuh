@@ -192,7 +192,7 @@ template <> struct IntCfg<double> {
 template <> struct IntCfg<float> {
     enum { G = 4 };
     static OOTS_HD float umax() { return 20.0f; }
-    static OOTS_HD float tolq() { return 2e-7f; }
+    static OOTS_HD float tolq() { return 1e-6f; }
     static OOTS_HD float zlin() { return 3e-3f; }
 };
 
@@ -364,15 +364,17 @@ OOTS_HD bool near_root_solution(const CellODE<Real> &C, Real xe, Real d0, Real D
 // First part of the integration: the closed forms.  Returns true when the
 // cell is done (photon-free, at its root, or slow enough for the linearised
 // step); otherwise F(x0), F'(x0) and f(x0) are left for the general part.
+// have_F: F0 and dF0 already hold F(x0) and F'(x0).
 template <typename Real, int NSMAX = MAX_SRC>
 OOTS_HD bool integrate_prelude(const CellODE<Real> &C, Real x0, Real h, Real sigma0, IntResult<Real> &R,
-                               Real &F0, Real &dF0, Real &f0)
+                               Real &F0, Real &dF0, Real &f0, bool have_F = false)
 {
     constexpr int G = IntCfg<Real>::G;
     R.x = x0;
     R.IR = Real(0);
     R.lnfav = -C.b0 * x0;
-    F0 = dF0 = f0 = Real(0);
+    if (!have_F) F0 = dF0 = Real(0);
+    f0 = Real(0);
     if (!(h > Real(0))) return true;
 
     // photon-free cell: du/dt = -c u^2, u = 1 - x (closed form)
@@ -398,7 +400,7 @@ OOTS_HD bool integrate_prelude(const CellODE<Real> &C, Real x0, Real h, Real sig
         return true;
     }
 
-    ode_F<Real, NSMAX>(C, x0, &F0, &dF0);
+    if (!have_F) ode_F<Real, NSMAX>(C, x0, &F0, &dF0);
     f0 = -F0 + C.c * (Real(1) - x0) * (Real(1) - x0);
     // at the root to within the rounding of f: x stays
     if (m_abs(f0) <= Real(32) * RealLimits<Real>::eps() * (m_abs(F0) + C.c * (Real(1) - x0) * (Real(1) - x0))) {

@@ -54,11 +54,14 @@ cudaError_t launch_sweep(const SweepParams<Real> &P, int shape, int mode, int nb
 enum { OP_RATEDT = 0, OP_HALF = 1, OP_FULL1 = 2, OP_FULL2 = 3, OP_GENERAL = 16 };
 // qrec: per queue slot the closed-form pass's rates and f(x0) of single-source
 // cells (queue_record_bytes each), so the general pass starts at the root
-// search; unused (may be null) when nsmax > 1
+// search.  rcache: 3 x total values per cell (transmitted fraction, F(x0),
+// F'(x0)) that the dt pass writes and the half step (A3) or full step (A2)
+// of the same substep reads when use_cache is set.  Both unused (may be null)
+// when nsmax > 1.
 template <typename Real>
 cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
                         const DevTable<Real> *tabs, int op, int nsmax, unsigned *queue, unsigned *qcount,
-                        Real *qrec, int gen_blocks, cudaStream_t s);
+                        Real *qrec, Real *rcache, int use_cache, int gen_blocks, cudaStream_t s);
 template <typename Real> size_t queue_record_bytes();
 template <typename Real> int cell_general_occupancy(int nsmax);
 // stage 0 also clears the queue lengths and the general passes' head counters

@@ -137,6 +137,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     long long total = 0;
     unsigned *d_queue = nullptr;       // cells left to the general pass (one entry per cell at most)
     Real *d_qrec = nullptr;            // their closed-form results (single-source launch sets)
+    Real *d_rcache = nullptr;          // per cell: transmitted fraction, F(x0), F'(x0) from the dt pass
     unsigned *d_qcount = nullptr;      // queue lengths of the half and full integrations
     int gen_blocks = 1;                // grid of the general pass
     int nblocks0 = 1, nblocks1 = 1;
@@ -162,6 +163,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         cudaFree(d_offsets);
         cudaFree(d_queue);
         cudaFree(d_qrec);
+        cudaFree(d_rcache);
         cudaFree(d_qcount);
     }
 
@@ -299,6 +301,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         if (total > 0xffffffffll) return fail(OOTS_E_INVAL, "%lld cells in one call (the queue holds 32-bit indices)", total);
         CU(cudaMalloc(&d_queue, (size_t)std::max(total, 1ll) * sizeof(unsigned)));
         if (nsmax <= 1) CU(cudaMalloc(&d_qrec, (size_t)std::max(total, 1ll) * queue_record_bytes<Real>()));
+        if (nsmax <= 1) CU(cudaMalloc(&d_rcache, (size_t)std::max(total, 1ll) * 3 * sizeof(Real)));
         CU(cudaMalloc(&d_qcount, 8 * sizeof(unsigned)));
         CU(cudaMemset(d_qcount, 0, 8 * sizeof(unsigned)));
         if (!jobs.empty()) {
@@ -355,17 +358,18 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         return OOTS_OK;
     }
 
-    int cell(cudaStream_t s, int op)
+    // use_cache: the dt pass ran earlier in this substep on the same state and columns
+    int cell(cudaStream_t s, int op, bool use_cache = false)
     {
         if (prof) prof->mark(0);
         CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op, nsmax, d_queue, d_qcount, d_qrec,
-                             gen_blocks, s));
+                             d_rcache, use_cache ? 1 : 0, gen_blocks, s));
         if (prof) prof->mark(op == OP_RATEDT ? OOTS_K_RATEDT : (op == OP_HALF ? OOTS_K_HALF : OOTS_K_FULL));
         if (op == OP_RATEDT) return OOTS_OK;
         // the cells no closed form settles, one warp each
         if (prof) prof->mark(0);
         CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op | OP_GENERAL, nsmax, d_queue,
-                             d_qcount, d_qrec, gen_blocks, s));
+                             d_qcount, d_qrec, d_rcache, 0, gen_blocks, s));
         if (prof) prof->mark(op == OP_HALF ? OOTS_K_HALF_GENERAL : OOTS_K_FULL_GENERAL);
         return OOTS_OK;
     }
@@ -399,11 +403,11 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         if (!fixed_dt && (rc = cell(s, OP_RATEDT))) return rc;
         if ((rc = fin(s, 0))) return rc;
         if (scheme == OOTS_A3) {
-            if ((rc = cell(s, OP_HALF))) return rc;
+            if ((rc = cell(s, OP_HALF, !fixed_dt))) return rc;
             if ((rc = sweep(s, 1, 0))) return rc;
             if ((rc = cell(s, OP_FULL2))) return rc;
         } else {
-            if ((rc = cell(s, OP_FULL1))) return rc;
+            if ((rc = cell(s, OP_FULL1, !fixed_dt))) return rc;
         }
         return fin(s, 1);
     }

@@ -9,7 +9,7 @@ what it computes quickly at this size:
 - x^{n+1} of sampled cells, integrated one by one from the GPU's own state
   and entry columns.
 The samples include the cells that moved most, which are the front cells the
-general pass integrates.  The mixed path is judged on the front-radius
+general pass integrates.  The mixed path is checked on the front-radius
 metrics against the FP64 path.
 """
 import numpy as np

@@ -2,7 +2,7 @@
 
 FP64 path: per-cell neutral fraction within 1e-9 (the tolerance of the
 FP64 plain method), columns and dt within 1e-10 relative.  Mixed path:
-judged on the error metrics (front radius, ionised volume, max |dx|).
+checked on the error metrics (front radius, ionised volume, max |dx|).
 """
 import math
 
