@@ -41,22 +41,8 @@ __device__ __forceinline__ int cell_rates(const GridDev<Real> &G, const Real *Nc
         const int i = X >= G.vtx[s][0] ? X - G.vtx[s][0] : G.vtx[s][0] - 1 - X;
         const int j = Y >= G.vtx[s][1] ? Y - G.vtx[s][1] : G.vtx[s][1] - 1 - Y;
         const int k = Z >= G.vtx[s][2] ? Z - G.vtx[s][2] : G.vtx[s][2] - 1 - Z;
-        const Real c0 = Real(i) + Real(0.5), c1 = Real(j) + Real(0.5), c2 = Real(k) + Real(0.5);
-        const Real r2 = c0 * c0 + c1 * c1 + c2 * c2;
-        const Real sf = m_sqrt(r2) / m_max(c0, m_max(c1, c2));
-        const Real N = Ncol[(long long)s * G.ncell + g];
-        r[s].Nin = N;
-        r[s].tab = G.tab[s];
-        if (r[s].tab < 0) {
-            // Q e^{-sigma0 N} / (n 4 pi r^2 ds) with r^2 ds in units of dx^3
-            r[s].A = G.qfac[s] * m_exp(-G.sigma0 * N) / (n * r2 * sf);
-            r[s].b = G.sigma0 * n * G.dx * sf;
-            r[s].p = Real(1);
-        } else {
-            r[s].A = G.qfac[s] / (n * r2 * sf);
-            r[s].b = n * G.dx * sf;
-            if (with_p) r[s].p = m_exp(tab_lnp(tabs[r[s].tab], N));
-        }
+        src_rate<Real>(r[s], G.qfac[s], G.tab[s], G.sigma0, G.dx, n, i, j, k, Ncol[(long long)s * G.ncell + g], tabs,
+                       with_p);
     }
     return G.nsrc;
 }

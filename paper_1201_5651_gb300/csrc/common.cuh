@@ -255,4 +255,29 @@ template <typename Real> struct SrcRate {
     int tab;              // -1: monochromatic; otherwise index of the table
 };
 
+// Rate parameters of one source for the cell (i,j,k) of its octant (vertex
+// at the origin) with entry column N: qfac = Q / (4 pi dx^3); the shell is
+// 4 pi r^2 ds with r^2 ds in units of dx^3.  with_p = false leaves p of a
+// tabulated source to the caller.
+template <typename Real>
+OOTS_HD __forceinline__ void src_rate(SrcRate<Real> &r, Real qfac, int tab, Real sigma0, Real dx, Real n, int i, int j,
+                                      int k, Real N, const DevTable<Real> *tabs, bool with_p = true)
+{
+    const Real c0 = Real(i) + Real(0.5), c1 = Real(j) + Real(0.5), c2 = Real(k) + Real(0.5);
+    const Real r2 = c0 * c0 + c1 * c1 + c2 * c2;
+    const Real sf = m_sqrt(r2) / m_max(c0, m_max(c1, c2));
+    r.Nin = N;
+    r.tab = tab;
+    if (tab < 0) {
+        // Q e^{-sigma0 N} / (n 4 pi r^2 ds)
+        r.A = qfac * m_exp(-sigma0 * N) / (n * r2 * sf);
+        r.b = sigma0 * n * dx * sf;
+        r.p = Real(1);
+    } else {
+        r.A = qfac / (n * r2 * sf);
+        r.b = n * dx * sf;
+        if (with_p) r.p = m_exp(tab_lnp(tabs[tab], N));
+    }
+}
+
 } // namespace oots
