@@ -48,7 +48,8 @@ class _Problem(ctypes.Structure):
                 ("tau0", ctypes.c_double), ("nH", ctypes.c_void_p), ("nsrc", ctypes.c_int),
                 ("vtx", ctypes.c_void_p), ("Q", ctypes.c_void_p), ("kind", ctypes.c_void_p),
                 ("tabL", ctypes.c_void_p), ("tabD1", ctypes.c_void_p), ("tabD2", ctypes.c_void_p),
-                ("K", ctypes.c_int), ("lnN_lo", ctypes.c_double), ("lnN_hi", ctypes.c_double)]
+                ("K", ctypes.c_int), ("lnN_lo", ctypes.c_double), ("lnN_hi", ctypes.c_double),
+                ("plane", ctypes.c_void_p)]
 
 
 class _Scheme(ctypes.Structure):
@@ -117,7 +118,10 @@ class Problem:
 
     def __init__(self, nx, ny, nz, dx, nH, sources, alpha=2.59e-13, sigma0=6.3e-18, tau0=0.6,
                  tables=None):
-        """sources: list of (pos(3 floats), Q, spectrum "mono"|"bb", T).
+        """sources: list of (pos(3 floats), Q, spectrum "mono"|"bb", T[, plane]).
+        plane (default -1, a point source at the vertex nearest pos) = 2*axis + back
+        makes a plane-parallel source whose rays run along +axis (back 0) or
+        -axis (back 1); its Q is a photon flux [cm^-2 s^-1] and pos is unused.
         tables: optional per-source (L, D1, D2) overriding the built table."""
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.ncell = self.nx * self.ny * self.nz
@@ -127,12 +131,17 @@ class Problem:
         self.vtx = np.zeros(3 * ns, np.int32)
         self.Q = np.zeros(ns)
         self.kind = np.zeros(ns, np.int32)
+        self.plane = np.full(ns, -1, np.int32)
         self.tabL = np.zeros(ns * TAB_K); self.tabD1 = np.zeros(ns * TAB_K); self.tabD2 = np.zeros(ns * TAB_K)
         n3 = (self.nx, self.ny, self.nz)
         for s, src in enumerate(sources):
-            pos, Q, spec, T = src
-            for q in range(3):
-                self.vtx[3 * s + q] = snap(pos[q], n3[q])
+            pos, Q, spec, T = src[:4]
+            self.plane[s] = int(src[4]) if len(src) > 4 else -1
+            if not -1 <= self.plane[s] <= 5:
+                raise ValueError(f"plane code {self.plane[s]}")
+            if self.plane[s] < 0:
+                for q in range(3):
+                    self.vtx[3 * s + q] = snap(pos[q], n3[q])
             self.Q[s] = Q
             if spec != "mono":
                 self.kind[s] = 1
@@ -146,14 +155,14 @@ class Problem:
         self.st = _Problem(self.nx, self.ny, self.nz, float(dx), float(alpha), float(sigma0), float(tau0),
                            self.nH.ctypes.data, self.nsrc, self.vtx.ctypes.data, self.Q.ctypes.data,
                            self.kind.ctypes.data, self.tabL.ctypes.data, self.tabD1.ctypes.data,
-                           self.tabD2.ctypes.data, TAB_K, TAB_LNN_LO, TAB_LNN_HI)
+                           self.tabD2.ctypes.data, TAB_K, TAB_LNN_LO, TAB_LNN_HI, self.plane.ctypes.data)
         self.dx = float(dx)
         self.alpha = float(alpha)
         self.sigma0 = float(sigma0)
 
     @classmethod
     def from_workload(cls, w, **kw):
-        srcs = [(s.pos, s.Q, s.spectrum, s.T) for s in w.sources]
+        srcs = [(s.pos, s.Q, s.spectrum, s.T, getattr(s, "plane", -1)) for s in w.sources]
         return cls(w.nx, w.ny, w.nz, w.dx, w.nH, srcs, alpha=w.alpha, sigma0=w.sigma0, tau0=w.tau0, **kw)
 
     # ---------------------------------------------------------------- trace

@@ -26,7 +26,11 @@
  *   - frequency-integrated rate tables for a blackbody source (Sect. 2, the
  *     paragraph on multi-frequency rates; Sect. 4);
  *   - brute-force long characteristics (exact voxel traversal), used only to
- *     bound the accuracy of the short characteristics.
+ *     bound the accuracy of the short characteristics;
+ *   - plane-parallel sources (a source at infinity whose rays run parallel to
+ *     a grid axis, the slab test of Sect. 3.1): the column to a cell is the sum
+ *     of n x dx of the cells before it on its row, and the rate of a cell is
+ *     the photon flux it removes per unit face area over n dx.
  *
  * Readings where the paper is silent (each is a parameter or a stated choice):
  *   - rate form: absorbed photons per atom per second
@@ -77,6 +81,11 @@ typedef struct {
     const double *tabD2;   /* per source, K values: d2 ln P / d (ln N)^2       */
     int K;                 /* table nodes                                      */
     double lnN_lo, lnN_hi; /* ln of the first and last node column [cm^-2]     */
+    const int *plane;      /* per source (NULL: all point sources): -1 for a
+                              vertex point source; 2*axis + back for a plane
+                              source whose rays run along +axis (back = 0) or
+                              -axis (back = 1).  A plane source's Q is its
+                              photon flux F_gamma [cm^-2 s^-1].                */
 } or_problem;
 
 typedef struct {
@@ -355,6 +364,51 @@ static void cell_geom(const or_problem *p, int s, int X, int Y, int Z,
     *sfac = sqrt(*r2) / cm;
 }
 
+/* -1 for a vertex point source, else the plane code 2*axis + back. */
+static int src_plane(const or_problem *p, int s) { return p->plane ? p->plane[s] : -1; }
+
+/* Ray segment ds through the cell (X,Y,Z) and the volume V_sh over which the
+ * photons it removes are shared, for source s:
+ *   point source: ds = dx |c|/max(c), V_sh = 4 pi r^2 ds (per unit Q);
+ *   plane source: ds = dx and V_sh = dx, the cell volume per unit face area
+ *                 (Q is then a flux per unit area). */
+static void src_shell(const or_problem *p, int s, int X, int Y, int Z, double *ds, double *Vsh)
+{
+    if (src_plane(p, s) >= 0) {
+        *ds = p->dx;
+        *Vsh = p->dx;
+        return;
+    }
+    int ijk[3]; double r2, sf;
+    cell_geom(p, s, X, Y, Z, ijk, &r2, &sf);
+    *ds = p->dx * sf;
+    *Vsh = 4.0 * OR_PI * r2 * p->dx * p->dx * *ds;
+}
+
+/* Photons per second source s emits into the grid: Q for a point source; for
+ * a plane source its flux times the area of the face it enters through. */
+static double src_emission(const or_problem *p, int s)
+{
+    int code = src_plane(p, s);
+    if (code < 0) return p->Q[s];
+    int n3[3] = {p->nx, p->ny, p->nz};
+    int axis = code / 2;
+    return p->Q[s] * (double)n3[(axis + 1) % 3] * (double)n3[(axis + 2) % 3] * p->dx * p->dx;
+}
+
+/* Cell (u, w) of row m, counted along the direction of travel of plane code
+ * `code`: u and w index the two transverse axes (axis+1, axis+2 mod 3). */
+static long plane_cell(const or_problem *p, int code, int m, int u, int w)
+{
+    int axis = code / 2, back = code & 1;
+    int n3[3] = {p->nx, p->ny, p->nz};
+    int G[3];
+    G[axis] = back ? n3[axis] - 1 - m : m;
+    G[(axis + 1) % 3] = u;
+    G[(axis + 2) % 3] = w;
+    return G[0] + (long)p->nx * (G[1] + (long)p->ny * G[2]);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Short-characteristics trace                                               */
 /* ------------------------------------------------------------------------ */
@@ -412,6 +466,25 @@ static double sc_interp(const or_problem *p, const int *v, const int *sg, const 
 void or_trace(const or_problem *p, int s, const double *x, double *Nin, double *dtau_out)
 {
     long ncell = (long)p->nx * p->ny * p->nz;
+    int code = src_plane(p, s);
+    if (code >= 0) {
+        /* rays parallel to the axis: each row is traced from the face the
+         * photons enter through, with no interpolation */
+        int n3[3] = {p->nx, p->ny, p->nz};
+        int axis = code / 2;
+        for (int w = 0; w < n3[(axis + 2) % 3]; w++)
+            for (int u = 0; u < n3[(axis + 1) % 3]; u++) {
+                double N = 0.0;
+                for (int m = 0; m < n3[axis]; m++) {
+                    long gi = plane_cell(p, code, m, u, w);
+                    double dN = p->nH[gi] * x[gi] * p->dx;
+                    Nin[gi] = N;
+                    if (dtau_out) dtau_out[gi] = p->sigma0 * dN;
+                    N += dN;
+                }
+            }
+        return;
+    }
     double *Nout = (double *)malloc(sizeof(double) * ncell);
     double *dtau = dtau_out ? dtau_out : (double *)malloc(sizeof(double) * ncell);
     const int *v = p->vtx + 3 * s;
@@ -748,10 +821,8 @@ static void cell_rates(const or_problem *p, int X, int Y, int Z, long gi, long n
 {
     double n = p->nH[gi];
     for (int s = 0; s < p->nsrc; s++) {
-        int ijk[3]; double r2, sf;
-        cell_geom(p, s, X, Y, Z, ijk, &r2, &sf);
-        double ds = p->dx * sf;
-        double Vsh = 4.0 * OR_PI * r2 * p->dx * p->dx * ds;
+        double ds, Vsh;
+        src_shell(p, s, X, Y, Z, &ds, &Vsh);
         double N = Nin[(long)s * ncell + gi];
         r[s].Nin = N;
         if (p->kind[s] == 0) {
@@ -866,17 +937,67 @@ void or_integrate_cells(const or_problem *p, long nq, const long *idx, const dou
 }
 
 /*
+ * A1 (Sect. 2.1, Eq. 3), one cell: integrate (x, attenuation) over dt from
+ * x0[gi] with the entry column nin frozen, store x(dt), and return the
+ * effective optical depth -ln<f> at nu0 that builds the column handed
+ * downstream, N_out = N_in - ln<f>/sigma0.  ds and Vsh as in src_shell.
+ */
+static double a1_cell(const or_problem *p, long gi, double nin, double ds, double Vsh,
+                      const double *x0, double dt, double *xout, double *budget)
+{
+    double n = p->nH[gi];
+    or_srcrate r;
+    r.Nin = nin;
+    if (p->kind[0] == 0) {
+        r.kind = 0;
+        r.A = p->Q[0] * exp(-p->sigma0 * nin) / (n * Vsh);
+        r.b = p->sigma0 * n * ds;
+    } else {
+        r.kind = 1;
+        r.A = p->Q[0] / (n * Vsh);
+        r.b = n * ds;
+        r.tab.L = p->tabL; r.tab.D1 = p->tabD1; r.tab.D2 = p->tabD2;
+        r.tab.K = p->K; r.tab.lnN_lo = p->lnN_lo; r.tab.lnN_hi = p->lnN_hi;
+    }
+    or_cell C = {1, &r, p->alpha * n, p->sigma0 * n * ds};
+    or_intres R = or_integrate_cell(&C, x0[gi], dt);
+    xout[gi] = R.x;
+    if (budget) {
+        double nV = n * p->dx * p->dx * p->dx;
+        budget[1] += nV * R.IF;
+        budget[2] += nV * (x0[gi] - R.x);
+        budget[3] += nV * R.IR;
+    }
+    return -R.lnfav;
+}
+
+/*
  * A1 (Sect. 2.1): one sweep per octant in which every cell, in causal order,
  * takes its entry column from the time-averaged columns of its upwind
  * neighbours, integrates (x, attenuation) over dt, and hands downstream the
  * column N_out = N_in - ln<f>/sigma0 built from its time-averaged
- * attenuation <f> at nu0 (Eq. 3).  Single source.
+ * attenuation <f> at nu0 (Eq. 3).  Single source.  For a plane source the
+ * causal order is along each row from the face the photons enter through.
  */
 static void a1_sweep(const or_problem *p, const double *x0, double dt, double *xout,
                      double *Nin_out, double *budget)
 {
     long ncell = (long)p->nx * p->ny * p->nz;
-    double V = p->dx * p->dx * p->dx;
+    int code = src_plane(p, 0);
+    if (code >= 0) {
+        int n3[3] = {p->nx, p->ny, p->nz};
+        int axis = code / 2;
+        for (int w = 0; w < n3[(axis + 2) % 3]; w++)
+            for (int u = 0; u < n3[(axis + 1) % 3]; u++) {
+                double N = 0.0;
+                for (int m = 0; m < n3[axis]; m++) {
+                    long gi = plane_cell(p, code, m, u, w);
+                    if (Nin_out) Nin_out[gi] = N;
+                    N += a1_cell(p, gi, N, p->dx, p->dx, x0, dt, xout, budget) / p->sigma0;
+                }
+            }
+        return;
+    }
     double *Nout = (double *)malloc(sizeof(double) * ncell);
     double *dtau = (double *)malloc(sizeof(double) * ncell);
     const int *v = p->vtx;
@@ -897,39 +1018,12 @@ static void a1_sweep(const or_problem *p, const double *x0, double dt, double *x
                                 sg[2] > 0 ? v[2] + k : v[2] - 1 - k};
                     long gi = G[0] + (long)p->nx * (G[1] + (long)p->ny * G[2]);
                     double nin = (m == 0) ? 0.0 : sc_interp(p, v, sg, ext, i, j, k, Nout, dtau);
-                    double n = p->nH[gi];
-                    double c0 = i + 0.5, c1 = j + 0.5, c2 = k + 0.5;
-                    double cm = c0 > c1 ? c0 : c1;
-                    cm = cm > c2 ? cm : c2;
-                    double r2 = c0 * c0 + c1 * c1 + c2 * c2;
-                    double ds = p->dx * sqrt(r2) / cm;
-                    double Vsh = 4.0 * OR_PI * r2 * p->dx * p->dx * ds;
-                    or_srcrate r;
-                    r.Nin = nin;
-                    if (p->kind[0] == 0) {
-                        r.kind = 0;
-                        r.A = p->Q[0] * exp(-p->sigma0 * nin) / (n * Vsh);
-                        r.b = p->sigma0 * n * ds;
-                    } else {
-                        r.kind = 1;
-                        r.A = p->Q[0] / (n * Vsh);
-                        r.b = n * ds;
-                        r.tab.L = p->tabL; r.tab.D1 = p->tabD1; r.tab.D2 = p->tabD2;
-                        r.tab.K = p->K; r.tab.lnN_lo = p->lnN_lo; r.tab.lnN_hi = p->lnN_hi;
-                    }
-                    or_cell C = {1, &r, p->alpha * n, p->sigma0 * n * ds};
-                    or_intres R = or_integrate_cell(&C, x0[gi], dt);
-                    double dtau_eff = -R.lnfav;          /* -ln <f> at nu0 */
-                    xout[gi] = R.x;
+                    double ds, Vsh;
+                    src_shell(p, 0, G[0], G[1], G[2], &ds, &Vsh);
+                    double dtau_eff = a1_cell(p, gi, nin, ds, Vsh, x0, dt, xout, budget);
                     if (Nin_out) Nin_out[gi] = nin;
                     Nout[gi] = nin + dtau_eff / p->sigma0;
                     dtau[gi] = dtau_eff;
-                    if (budget) {
-                        double nV = n * V;
-                        budget[1] += nV * R.IF;
-                        budget[2] += nV * (x0[gi] - R.x);
-                        budget[3] += nV * R.IR;
-                    }
                 }
             }
         }
@@ -941,7 +1035,8 @@ static void a1_sweep(const or_problem *p, const double *x0, double dt, double *x
 /*
  * One substep of the chosen scheme, advancing x in place from t to t + dt
  * (dt from Eq. 4 or fixed, capped at t_end - t).  Returns dt.
- *   budget (4 doubles, overwritten): emitted sum Q dt, absorbed, new ions,
+ *   budget (4 doubles, overwritten): emitted photons (sum Q dt; a plane
+ *   source's flux times its entry face), absorbed, new ions,
  *   recombinations (the last three from the full-step integration);
  *   Nin1 (optional, nsrc x ncell): the entry columns of the first trace.
  * A3 (Sect. 2.2, Fig. 1): trace x^n; dt; x_half = X(x^n, N^1, dt/2); trace
@@ -982,7 +1077,7 @@ double or_substep(const or_problem *p, const or_scheme *sc, double *x, double *t
     } else {
         a1_sweep(p, x, dt, xn, (need_trace || !Nin1) ? NULL : N1, bud);
     }
-    for (int s = 0; s < S; s++) bud[0] += p->Q[s] * dt;
+    for (int s = 0; s < S; s++) bud[0] += src_emission(p, s) * dt;
     memcpy(x, xn, sizeof(double) * ncell);
     *t += dt;
     if (budget) memcpy(budget, bud, sizeof(bud));
@@ -1000,6 +1095,14 @@ double or_substep(const or_problem *p, const or_scheme *sc, double *x, double *t
  */
 void or_long_char(const or_problem *p, int s, const double *x, double *Ncentre)
 {
+    if (src_plane(p, s) >= 0) {
+        /* the ray to a cell centre runs along its row: whole cells before it,
+         * half of its own */
+        long ncell = (long)p->nx * p->ny * p->nz;
+        or_trace(p, s, x, Ncentre, NULL);
+        for (long gi = 0; gi < ncell; gi++) Ncentre[gi] += 0.5 * p->nH[gi] * x[gi] * p->dx;
+        return;
+    }
     const int *v = p->vtx + 3 * s;
     int n3[3] = {p->nx, p->ny, p->nz};
     for (int Z = 0; Z < p->nz; Z++)

@@ -13,7 +13,10 @@ Workloads (sizes, distributions and seeds):
     P(k) ~ k^-3, blackbody source at the centre vertex;
   * ``clumpy``: lognormal density times spherical clumps;
   * ``batch``: many uniform grids of uneven sizes, densities and rates;
-  * ``multisource``: lognormal density with many blackbody sources.
+  * ``multisource``: lognormal density with many blackbody sources;
+  * ``planar_slab``: the plane-parallel slab of Sect. 3.1 (source at infinity,
+    uniform hydrogen, no recombinations);
+  * ``plane_random``: small random grid lit by a plane-parallel source.
 """
 from __future__ import annotations
 
@@ -36,6 +39,8 @@ class Source:
     Q: float              # ionising photons per second
     spectrum: str = "mono"  # "mono" or "bb"
     T: float = 0.0        # blackbody temperature [K] for "bb"
+    plane: int = -1       # -1: point source; else 2*axis + back, a plane-parallel source whose
+                          # rays run along +axis (back 0) or -axis (back 1); Q is then a flux [cm^-2 s^-1]
 
 
 @dataclasses.dataclass
@@ -204,5 +209,46 @@ def small_random(n: int = 12, seed: int = 7, nsrc: int = 1, spectrum: str = "mon
         srcs.append(Source(pos, Q * float(rng.uniform(0.5, 2.0)), spectrum, T if spectrum == "bb" else 0.0))
     L = box_rs * stromgren_radius(Q, 100.0)
     w = Workload("small_random", n, ny, nz, L / n, nH, x0, srcs)
+    w.t_rec = 1.0 / (ALPHA_B * 100.0)
+    return w
+
+
+def planar_slab(n: int = 100, F: float = 1e9, n_H: float = 100.0, dtau: float = 10.0, ny: int = 1, nz: int = 1,
+                axis: int = 0, back: int = 0) -> Workload:
+    """Sect. 3.1: a slab of n cells of uniform hydrogen lit from one face by a
+    monochromatic plane-parallel flux F [cm^-2 s^-1], cell optical depth dtau
+    at x = 1, recombinations off (alpha = 0).  The cell count n lies along
+    `axis`; the grid is n x ny x nz cells in that axis order."""
+    dx = dtau / (SIGMA0 * n_H)
+    dims = [ny, nz]
+    shape_xyz = [0, 0, 0]
+    shape_xyz[axis] = n
+    shape_xyz[(axis + 1) % 3] = dims[0]
+    shape_xyz[(axis + 2) % 3] = dims[1]
+    nx_, ny_, nz_ = shape_xyz
+    full = np.full((nz_, ny_, nx_), n_H, dtype=np.float64)
+    w = Workload("planar_slab", nx_, ny_, nz_, dx, full, np.full((nz_, ny_, nx_), X_NEUTRAL),
+                 [Source((0.0, 0.0, 0.0), F, "mono", 0.0, 2 * axis + back)], alpha=0.0, uniform_n=n_H)
+    return w
+
+
+def plane_random(n: int = 12, seed: int = 11, axis: int = 0, back: int = 0, F: float = 1e9,
+                 spectrum: str = "mono", T: float = 4e4, sigma_ln: float = 1.0, x_lo: float = 0.0,
+                 dtau: float = 2.0, ny: Optional[int] = None, nz: Optional[int] = None,
+                 point_Q: float = 0.0) -> Workload:
+    """Small non-cubic grid with a lognormal-like random density and random
+    neutral fractions in [x_lo, 1], lit by one plane-parallel source (flux F)
+    and, if point_Q > 0, also by a point source at a random vertex.  The cell
+    optical depth at the mean density and x = 1 is dtau."""
+    rng = np.random.default_rng(seed)
+    ny = n if ny is None else ny
+    nz = n if nz is None else nz
+    nH = 100.0 * np.exp(sigma_ln * rng.standard_normal((nz, ny, n)) - 0.5 * sigma_ln ** 2)
+    x0 = rng.uniform(x_lo, 1.0, (nz, ny, n))
+    srcs = [Source((0.0, 0.0, 0.0), F, spectrum, T if spectrum == "bb" else 0.0, 2 * axis + back)]
+    if point_Q > 0:
+        pos = (float(rng.integers(0, n + 1)), float(rng.integers(0, ny + 1)), float(rng.integers(0, nz + 1)))
+        srcs.append(Source(pos, point_Q, spectrum, T if spectrum == "bb" else 0.0))
+    w = Workload("plane_random", n, ny, nz, dtau / (SIGMA0 * 100.0), nH, x0, srcs)
     w.t_rec = 1.0 / (ALPHA_B * 100.0)
     return w
