@@ -132,6 +132,21 @@ int oots_set_physics(oots_ctx *ctx, double alpha_B, double sigma0, double tau0, 
  * receives the source index.  At most 64 sources.  Errors: E_INVAL. */
 int oots_add_source(oots_ctx *ctx, const double pos_cells[3], double Q, int spectrum, double T_bb, int *id);
 
+/* Add a plane-parallel source: a source at infinity whose rays run parallel
+ * to grid axis `axis` (0: x, 1: y, 2: z), along +axis (direction = +1,
+ * entering through the face at index 0) or -axis (direction = -1, entering
+ * through the face at index n-1), with photon flux F [photons cm^-2 s^-1]
+ * across that face and spectrum OOTS_MONO or OOTS_BLACKBODY (T_bb [K]).  This
+ * is the source of the slab test of Sect. 3.1.  A cell's entry column is the
+ * sum of n x dx over the cells before it on its row; its rate shares the
+ * photons the row loses in it over the cell volume per unit face area, dx.
+ * The photon budget counts F times the face area as emitted.  Plane and point
+ * sources mix freely (A1 takes a single source of either kind).  *id
+ * (optional) receives the source index.  Errors: E_INVAL (axis, direction,
+ * F <= 0 or not finite, spectrum, T_bb outside [1e3, 1e6], more than 64
+ * sources), E_STATE (no grid). */
+int oots_add_plane_source(oots_ctx *ctx, int axis, int direction, double F, int spectrum, double T_bb, int *id);
+
 /* Remove all sources. */
 int oots_clear_sources(oots_ctx *ctx);
 
@@ -182,6 +197,8 @@ int oots_run_substeps(oots_ctx *ctx, long long n, double t_end);
 #define OOTS_K_IMPLICIT  8   /* implicit sweep (A1)                      */
 #define OOTS_K_HALF_GENERAL 9  /* half step, cells no closed form settles (one warp each) */
 #define OOTS_K_FULL_GENERAL 10 /* full step, cells no closed form settles (one warp each) */
+#define OOTS_K_PLANE_TRACE 11  /* columns of the plane-parallel sources (either trace) */
+#define OOTS_K_PLANE_IMPLICIT 12 /* A1 row integration of a plane-parallel source */
 int oots_profile_substep(oots_ctx *ctx, int *kinds, double *ms, int nmax, int *n_out);
 
 /* ---- read-back --------------------------------------------------------------------------- */

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 LIBDIR = os.path.join(HERE, "_lib")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
-SOURCES = ["oots_capi.cu", "sweep_f.cu", "sweep_d.cu", "cell.cu", "tables.cpp", "noalloc.cu"]
+SOURCES = ["oots_capi.cu", "sweep_f.cu", "sweep_d.cu", "cell.cu", "tables.cpp", "noalloc.cu", "plane.cu"]
 
 
 def lib_path() -> str:

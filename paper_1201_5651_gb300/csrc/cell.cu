@@ -41,8 +41,8 @@ __device__ __forceinline__ int cell_rates(const GridDev<Real> &G, const Real *Nc
         const int i = X >= G.vtx[s][0] ? X - G.vtx[s][0] : G.vtx[s][0] - 1 - X;
         const int j = Y >= G.vtx[s][1] ? Y - G.vtx[s][1] : G.vtx[s][1] - 1 - Y;
         const int k = Z >= G.vtx[s][2] ? Z - G.vtx[s][2] : G.vtx[s][2] - 1 - Z;
-        src_rate<Real>(r[s], G.qfac[s], G.tab[s], G.sigma0, G.dx, n, i, j, k, Ncol[(long long)s * G.ncell + g], tabs,
-                       with_p);
+        src_rate<Real>(r[s], G.qfac[s], G.tab[s], G.sigma0, G.dx, n, G.pcode[s] != 0, i, j, k,
+                       Ncol[(long long)s * G.ncell + g], tabs, with_p);
     }
     return G.nsrc;
 }

@@ -257,24 +257,30 @@ template <typename Real> struct SrcRate {
 
 // Rate parameters of one source for the cell (i,j,k) of its octant (vertex
 // at the origin) with entry column N: qfac = Q / (4 pi dx^3); the shell is
-// 4 pi r^2 ds with r^2 ds in units of dx^3.  with_p = false leaves p of a
+// 4 pi r^2 ds with r^2 ds in units of dx^3.  A plane source (plane = true;
+// i, j, k unused) has ds = dx and shares the photons it loses over the cell's
+// volume per unit face area, dx: qfac = F / dx.  with_p = false leaves p of a
 // tabulated source to the caller.
 template <typename Real>
-OOTS_HD __forceinline__ void src_rate(SrcRate<Real> &r, Real qfac, int tab, Real sigma0, Real dx, Real n, int i, int j,
-                                      int k, Real N, const DevTable<Real> *tabs, bool with_p = true)
+OOTS_HD __forceinline__ void src_rate(SrcRate<Real> &r, Real qfac, int tab, Real sigma0, Real dx, Real n, bool plane,
+                                      int i, int j, int k, Real N, const DevTable<Real> *tabs, bool with_p = true)
 {
-    const Real c0 = Real(i) + Real(0.5), c1 = Real(j) + Real(0.5), c2 = Real(k) + Real(0.5);
-    const Real r2 = c0 * c0 + c1 * c1 + c2 * c2;
-    const Real sf = m_sqrt(r2) / m_max(c0, m_max(c1, c2));
+    Real sf = Real(1), den = n;   // den = n V_sh in units of 4 pi dx^3 (point) or dx (plane)
+    if (!plane) {
+        const Real c0 = Real(i) + Real(0.5), c1 = Real(j) + Real(0.5), c2 = Real(k) + Real(0.5);
+        const Real r2 = c0 * c0 + c1 * c1 + c2 * c2;
+        sf = m_sqrt(r2) / m_max(c0, m_max(c1, c2));
+        den = n * r2 * sf;
+    }
     r.Nin = N;
     r.tab = tab;
     if (tab < 0) {
-        // Q e^{-sigma0 N} / (n 4 pi r^2 ds)
-        r.A = qfac * m_exp(-sigma0 * N) / (n * r2 * sf);
+        // Q e^{-sigma0 N} / (n V_sh)
+        r.A = qfac * m_exp(-sigma0 * N) / den;
         r.b = sigma0 * n * dx * sf;
         r.p = Real(1);
     } else {
-        r.A = qfac / (n * r2 * sf);
+        r.A = qfac / den;
         r.b = n * dx * sf;
         if (with_p) r.p = m_exp(tab_lnp(tabs[tab], N));
     }

@@ -377,9 +377,23 @@ OOTS_HD bool integrate_prelude(const CellODE<Real> &C, Real x0, Real h, Real sig
     f0 = Real(0);
     if (!(h > Real(0))) return true;
 
-    // photon-free cell: du/dt = -c u^2, u = 1 - x (closed form)
+    // photon-free cell: du/dt = -c u^2, u = 1 - x (closed form).  A source
+    // counts only if it can move x by more than a thousandth of the rounding
+    // over h: its rate is at most A b x (monochromatic) or A p sigma0 b x
+    // (tabulated: no cross-section exceeds sigma0), so below that bound its
+    // effect is dropped.  This also keeps subnormal rates (a cell hundreds of
+    // optical depths down a row, with no recombinations to hold it) out of the
+    // quadrature, whose 1/D they would overflow.  The exception is A1 with
+    // recombinations (b0 > 0, c > 0): the attenuation average below is a fixed
+    // Gauss rule on the recombination trajectory, exact only when x stays put,
+    // so any nonzero rate keeps the full integration and its exact average.
     bool lit = false;
-    for (int i = 0; i < NSMAX && i < C.ns; i++) lit |= (C.r[i].A > Real(0));
+    const bool keep_any = C.b0 > Real(0) && C.c > Real(0);
+    for (int i = 0; i < NSMAX && i < C.ns; i++) {
+        const SrcRate<Real> &r = C.r[i];
+        const Real amp = r.tab < 0 ? r.A * r.b : r.A * r.p * sigma0 * r.b;
+        lit |= (amp * h > Real(1e-3) * RealLimits<Real>::eps()) || (keep_any && r.A > Real(0));
+    }
     if (!lit) {
         Real u0 = Real(1) - x0;
         Real u = u0 / (Real(1) + C.c * u0 * h);

@@ -49,6 +49,15 @@ template <typename Real> bool sweep_shape_ok(int shape);              // fits th
 template <typename Real>
 cudaError_t launch_sweep(const SweepParams<Real> &P, int shape, int mode, int nblocks, cudaStream_t s);
 
+// Plane-parallel sources: which = 0 traces x into N1, 1 traces xh into N2;
+// implicit = 1 runs the A1 row integration instead (single source).  nthreads
+// is the sum of plane_job_threads over the jobs, whose `first` fields are the
+// running sums.
+long long plane_job_threads(int code, long long rows);
+template <typename Real>
+cudaError_t launch_plane(const GridDev<Real> *grids, const PlaneJob *jobs, int njobs, long long nthreads,
+                         const DevTable<Real> *tabs, int which, int implicit, cudaStream_t s);
+
 // Per-cell passes.  HALF and FULL run as a closed-form pass over all cells
 // followed by the general pass (op | OP_GENERAL) over the queued cells.
 enum { OP_RATEDT = 0, OP_HALF = 1, OP_FULL1 = 2, OP_FULL2 = 3, OP_GENERAL = 16 };

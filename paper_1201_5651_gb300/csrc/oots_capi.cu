@@ -48,10 +48,21 @@ void oots_set_error_text(const char *msg) { g_err = msg; }
 struct SourceH {
     double pos[3];
     int v[3];
-    double Q;
+    double Q;              // photons per second; a plane source's flux per unit area
     int spectrum;
     double T;
+    int pcode = 0;         // 0: vertex point source; 1 + 2*axis + back: plane source
 };
+
+// Photons per second a source sends into the grid: a plane source's flux
+// times the area of the face it enters through.
+static double source_emission(const SourceH &S, int nx, int ny, int nz, double dx)
+{
+    if (!S.pcode) return S.Q;
+    const int n3[3] = {nx, ny, nz};
+    const int axis = (S.pcode - 1) >> 1;
+    return S.Q * (double)n3[(axis + 1) % 3] * (double)n3[(axis + 2) % 3] * dx * dx;
+}
 
 // Optional per-launch timing (oots_profile_substep): events around each launch.
 struct LaunchProfiler {
@@ -131,6 +142,9 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     long long ntiles = 0;
     unsigned *d_sync = nullptr;        // [0] ticket, [1] done (zeroed per sweep), [16] epoch (persistent)
     unsigned long long *d_faces = nullptr;
+    PlaneJob *d_pjobs = nullptr;       // plane-parallel sources
+    int npjobs = 0;
+    long long plane_threads = 0;
     DevTable<Real> *d_tabs = nullptr;
     std::vector<void *> tabmem;
     long long *d_offsets = nullptr;
@@ -158,6 +172,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         cudaFree(d_items);
         cudaFree(d_sync);
         cudaFree(d_faces);
+        cudaFree(d_pjobs);
         cudaFree(d_tabs);
         for (void *p : tabmem) cudaFree(p);
         cudaFree(d_offsets);
@@ -213,6 +228,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
 
         std::vector<GridDev<Real>> grids(cs.size());
         std::vector<Job> jobs;
+        std::vector<PlaneJob> pjobs;
         std::vector<TileItem> items;
         std::vector<DevTable<Real>> tabs;
         std::vector<long long> offs(cs.size());
@@ -239,8 +255,9 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
             G.st = c->d_st;
             for (int s = 0; s < G.nsrc; s++) {
                 const SourceH &S = c->src[s];
-                for (int a = 0; a < 3; a++) G.vtx[s][a] = S.v[a];
-                G.qfac[s] = Real(S.Q / (4.0 * M_PI * c->dx * c->dx * c->dx));
+                for (int a = 0; a < 3; a++) G.vtx[s][a] = S.pcode ? 0 : S.v[a];
+                G.qfac[s] = S.pcode ? Real(S.Q / c->dx) : Real(S.Q / (4.0 * M_PI * c->dx * c->dx * c->dx));
+                G.pcode[s] = (unsigned char)S.pcode;
                 if (S.spectrum == OOTS_MONO) G.tab[s] = -1;
                 else {
                     DevTable<Real> T;
@@ -250,6 +267,19 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
                     tabs.push_back(T);
                 }
                 const int n3[3] = {c->nx, c->ny, c->nz};
+                if (S.pcode) {
+                    PlaneJob P;
+                    memset(&P, 0, sizeof(P));
+                    P.grid = (int)g;
+                    P.src = s;
+                    P.code = S.pcode - 1;
+                    const int axis = P.code >> 1;
+                    P.rows = (long long)n3[(axis + 1) % 3] * n3[(axis + 2) % 3];
+                    P.first = plane_threads;
+                    plane_threads += plane_job_threads(P.code, P.rows);
+                    pjobs.push_back(P);
+                    continue;
+                }
                 for (int o = 0; o < 8; o++) {
                     Job J;
                     memset(&J, 0, sizeof(J));
@@ -316,6 +346,11 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
             CU(cudaMalloc(&d_faces, fbytes));
             CU(cudaMemset(d_faces, 0, fbytes));
         }
+        if (!pjobs.empty()) {
+            CU(cudaMalloc(&d_pjobs, pjobs.size() * sizeof(PlaneJob)));
+            CU(cudaMemcpy(d_pjobs, pjobs.data(), pjobs.size() * sizeof(PlaneJob), cudaMemcpyHostToDevice));
+            npjobs = (int)pjobs.size();
+        }
         if (!tabs.empty()) {
             CU(cudaMalloc(&d_tabs, tabs.size() * sizeof(DevTable<Real>)));
             CU(cudaMemcpy(d_tabs, tabs.data(), tabs.size() * sizeof(DevTable<Real>), cudaMemcpyHostToDevice));
@@ -348,13 +383,21 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         return P;
     }
 
+    // trace (mode 0) or A1 implicit sweep (mode 1) of every source: point
+    // sources by the wavefront sweep, plane sources row by row
     int sweep(cudaStream_t s, int which, int mode)
     {
-        if (nitems == 0) return OOTS_OK;
-        CU(cudaMemsetAsync(d_sync, 0, 2 * sizeof(unsigned), s));   // ticket and done; the epoch persists
-        if (prof) prof->mark(0);
-        CU(launch_sweep<Real>(params(which), shape, mode, mode == 0 ? nblocks0 : nblocks1, s));
-        if (prof) prof->mark(mode == 1 ? OOTS_K_IMPLICIT : (which == 0 ? OOTS_K_SWEEP1 : OOTS_K_SWEEP2));
+        if (nitems > 0) {
+            CU(cudaMemsetAsync(d_sync, 0, 2 * sizeof(unsigned), s));   // ticket and done; the epoch persists
+            if (prof) prof->mark(0);
+            CU(launch_sweep<Real>(params(which), shape, mode, mode == 0 ? nblocks0 : nblocks1, s));
+            if (prof) prof->mark(mode == 1 ? OOTS_K_IMPLICIT : (which == 0 ? OOTS_K_SWEEP1 : OOTS_K_SWEEP2));
+        }
+        if (npjobs > 0) {
+            if (prof) prof->mark(0);
+            CU(launch_plane<Real>(d_grids, d_pjobs, npjobs, plane_threads, d_tabs, which, mode, s));
+            if (prof) prof->mark(mode == 1 ? OOTS_K_PLANE_IMPLICIT : OOTS_K_PLANE_TRACE);
+        }
         return OOTS_OK;
     }
 
@@ -517,7 +560,7 @@ static int prepare(oots_ctx *c)
     c->h_st.K3 = c->crit.K3;
     c->h_st.K4 = c->crit.K4;
     double sq = 0.0;
-    for (auto &s : c->src) sq += s.Q;
+    for (auto &s : c->src) sq += source_emission(s, c->nx, c->ny, c->nz, c->dx);
     c->h_st.sumQ = sq;
     c->h_st.cell_volume = c->dx * c->dx * c->dx;
     if ((rc = push_state(c))) return rc;
@@ -764,6 +807,30 @@ int oots_add_source(oots_ctx *c, const double pos[3], double Q, int spectrum, do
     S.spectrum = spectrum;
     S.T = T_bb;
     if (spectrum == OOTS_BLACKBODY) host_table(1, T_bb, c->sigma0);   // build now, off the hot path
+    c->src.push_back(S);
+    if (id) *id = (int)c->src.size() - 1;
+    drop_solo(c);
+    return OOTS_OK;
+}
+
+int oots_add_plane_source(oots_ctx *c, int axis, int direction, double F, int spectrum, double T_bb, int *id)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (c->ncell == 0) return fail(OOTS_E_STATE, "no grid");
+    if (axis < 0 || axis > 2) return fail(OOTS_E_INVAL, "plane source axis %d (0..2)", axis);
+    if (direction != 1 && direction != -1) return fail(OOTS_E_INVAL, "plane source direction %d (+1 or -1)", direction);
+    if (!(F > 0) || !std::isfinite(F)) return fail(OOTS_E_INVAL, "plane source flux %g", F);
+    if (spectrum != OOTS_MONO && spectrum != OOTS_BLACKBODY) return fail(OOTS_E_INVAL, "spectrum %d", spectrum);
+    if (spectrum == OOTS_BLACKBODY && !(T_bb >= 1e3 && T_bb <= 1e6)) return fail(OOTS_E_INVAL, "blackbody temperature %g", T_bb);
+    if ((int)c->src.size() >= MAX_SRC) return fail(OOTS_E_INVAL, "at most %d sources", (int)MAX_SRC);
+    SourceH S;
+    memset(S.pos, 0, sizeof(S.pos));
+    memset(S.v, 0, sizeof(S.v));
+    S.Q = F;
+    S.spectrum = spectrum;
+    S.T = T_bb;
+    S.pcode = 1 + 2 * axis + (direction < 0 ? 1 : 0);
+    if (spectrum == OOTS_BLACKBODY) host_table(1, T_bb, c->sigma0);
     c->src.push_back(S);
     if (id) *id = (int)c->src.size() - 1;
     drop_solo(c);

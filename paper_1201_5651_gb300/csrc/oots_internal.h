@@ -22,6 +22,19 @@ struct Job {
     long long tile_base;   // index of tile (0,0,0) in the flag and face arrays
 };
 
+// One plane-parallel source of one grid (a source at infinity whose rays run
+// along a grid axis, Sect. 3.1): its rows are traced independently.  Rows of
+// axis 0 take one warp each (a warp scan along the contiguous row); rows of
+// axes 1 and 2 one thread each (neighbouring threads hold neighbouring x).
+struct PlaneJob {
+    int grid;              // index into the launch's grid array
+    int src;               // source index within the grid
+    int code;              // 2*axis + back: rays along +axis (back 0) or -axis (back 1)
+    int pad;
+    long long rows;        // rows of cells parallel to the axis
+    long long first;       // first thread of the job in the launch (a multiple of 32)
+};
+
 // One tile of a job, ordered in the work list by tile diagonal I+J+K.
 struct TileItem { int job; unsigned short I, J, K, pad; };
 
@@ -58,8 +71,9 @@ template <typename Real> struct GridDev {
     Real *N2;                 // entry columns of the second trace, nsrc x ncell
     int nsrc;
     int vtx[MAX_SRC][3];
-    Real qfac[MAX_SRC];       // Q / (4 pi dx^3)
+    Real qfac[MAX_SRC];       // Q / (4 pi dx^3); a plane source's flux F / dx
     int tab[MAX_SRC];         // -1 monochromatic, else table index
+    unsigned char pcode[MAX_SRC];  // 0: vertex point source; 1 + 2*axis + back: plane source (qfac = F/dx)
     DevState *st;
 };
 

@@ -38,10 +38,10 @@ EXPORTS = [
     "oots_set_neutral_fraction_device", "oots_get_neutral_fraction_device", "oots_synchronize",
     "oots_batch_create", "oots_batch_advance", "oots_batch_destroy", "oots_set_tile_shape",
     "oots_tile_shape_info", "oots_debug_set", "oots_version", "oots_run_substeps", "oots_profile_substep",
-    "oots_trace_noalloc",
+    "oots_trace_noalloc", "oots_add_plane_source",
 ]
 KERNEL_KINDS = {1: "sweep1", 2: "ratedt", 3: "final0", 4: "half", 5: "sweep2", 6: "full", 7: "final1", 8: "implicit",
-                9: "half_general", 10: "full_general"}
+                9: "half_general", 10: "full_general", 11: "plane_trace", 12: "plane_implicit"}
 
 
 class OotsError(RuntimeError):
@@ -92,6 +92,7 @@ def load(build_if_missing: bool = True):
         "oots_set_neutral_fraction": ([vp, vp, dp], ip),
         "oots_set_physics": ([vp, dp, dp, dp, dp], ip),
         "oots_add_source": ([vp, P(dp), dp, ip, dp, P(ip)], ip),
+        "oots_add_plane_source": ([vp, ip, ip, dp, ip, dp, P(ip)], ip),
         "oots_clear_sources": ([vp], ip),
         "oots_set_scheme": ([vp, ip, P(dtcrit)], ip),
         "oots_dtcrit_preset": ([ip, ip, P(dtcrit)], ip),
@@ -230,6 +231,14 @@ class Context:
         self._c(self.lib.oots_add_source(self.h, p, float(Q), sp, float(T), ctypes.byref(i)))
         return i.value
 
+    def add_plane_source(self, axis, direction, F, spectrum="mono", T=0.0):
+        """Plane-parallel source: rays along +axis (direction 1) or -axis (-1), flux F [cm^-2 s^-1]."""
+        i = ctypes.c_int()
+        sp = OOTS_MONO if spectrum in ("mono", OOTS_MONO) else OOTS_BLACKBODY
+        self._c(self.lib.oots_add_plane_source(self.h, int(axis), int(direction), float(F), sp, float(T),
+                                               ctypes.byref(i)))
+        return i.value
+
     def clear_sources(self):
         return self._c(self.lib.oots_clear_sources(self.h))
 
@@ -328,7 +337,11 @@ class Context:
             c.set_density(w.nH)
         c.set_neutral_fraction(w.x0)
         for s in w.sources:
-            c.add_source(s.pos, s.Q, s.spectrum, s.T)
+            code = getattr(s, "plane", -1)
+            if code >= 0:
+                c.add_plane_source(code // 2, -1 if code & 1 else 1, s.Q, s.spectrum, s.T)
+            else:
+                c.add_source(s.pos, s.Q, s.spectrum, s.T)
         if crit:
             c.set_scheme(scheme, **crit)
         return c
