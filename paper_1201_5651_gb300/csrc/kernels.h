@@ -50,13 +50,14 @@ template <typename Real>
 cudaError_t launch_sweep(const SweepParams<Real> &P, int shape, int mode, int nblocks, cudaStream_t s);
 
 // Plane-parallel sources: which = 0 traces x into N1, 1 traces xh into N2;
-// implicit = 1 runs the A1 row integration instead (single source).  nthreads
-// is the sum of plane_job_threads over the jobs, whose `first` fields are the
-// running sums.
+// implicit = 1 runs the A1 row integration instead (single source).  The jobs
+// along x come first (nrow0 of them, threads0 threads); nthreads is the sum
+// of plane_job_threads over all jobs, whose `first` fields are the running
+// sums.
 long long plane_job_threads(int code, long long rows);
 template <typename Real>
-cudaError_t launch_plane(const GridDev<Real> *grids, const PlaneJob *jobs, int njobs, long long nthreads,
-                         const DevTable<Real> *tabs, int which, int implicit, cudaStream_t s);
+cudaError_t launch_plane(const GridDev<Real> *grids, const PlaneJob *jobs, int njobs, int nrow0, long long nthreads,
+                         long long threads0, const DevTable<Real> *tabs, int which, int implicit, cudaStream_t s);
 
 // Per-cell passes.  HALF and FULL run as a closed-form pass over all cells
 // followed by the general pass (op | OP_GENERAL) over the queued cells.

@@ -143,8 +143,8 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     unsigned *d_sync = nullptr;        // [0] ticket, [1] done (zeroed per sweep), [16] epoch (persistent)
     unsigned long long *d_faces = nullptr;
     PlaneJob *d_pjobs = nullptr;       // plane-parallel sources
-    int npjobs = 0;
-    long long plane_threads = 0;
+    int npjobs = 0, nrow0 = 0;         // jobs; of them, rows along x (first in the array)
+    long long plane_threads = 0, threads0 = 0;
     DevTable<Real> *d_tabs = nullptr;
     std::vector<void *> tabmem;
     long long *d_offsets = nullptr;
@@ -275,8 +275,6 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
                     P.code = S.pcode - 1;
                     const int axis = P.code >> 1;
                     P.rows = (long long)n3[(axis + 1) % 3] * n3[(axis + 2) % 3];
-                    P.first = plane_threads;
-                    plane_threads += plane_job_threads(P.code, P.rows);
                     pjobs.push_back(P);
                     continue;
                 }
@@ -347,6 +345,15 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
             CU(cudaMemset(d_faces, 0, fbytes));
         }
         if (!pjobs.empty()) {
+            // rows along x first (their trace kernel differs), then the rest
+            std::stable_sort(pjobs.begin(), pjobs.end(), [](const PlaneJob &a, const PlaneJob &b) {
+                return (a.code >> 1 != 0) < (b.code >> 1 != 0);
+            });
+            for (auto &P : pjobs) {
+                if ((P.code >> 1) == 0) { nrow0++; threads0 += plane_job_threads(P.code, P.rows); }
+                P.first = plane_threads;
+                plane_threads += plane_job_threads(P.code, P.rows);
+            }
             CU(cudaMalloc(&d_pjobs, pjobs.size() * sizeof(PlaneJob)));
             CU(cudaMemcpy(d_pjobs, pjobs.data(), pjobs.size() * sizeof(PlaneJob), cudaMemcpyHostToDevice));
             npjobs = (int)pjobs.size();
@@ -395,7 +402,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         }
         if (npjobs > 0) {
             if (prof) prof->mark(0);
-            CU(launch_plane<Real>(d_grids, d_pjobs, npjobs, plane_threads, d_tabs, which, mode, s));
+            CU(launch_plane<Real>(d_grids, d_pjobs, npjobs, nrow0, plane_threads, threads0, d_tabs, which, mode, s));
             if (prof) prof->mark(mode == 1 ? OOTS_K_PLANE_IMPLICIT : OOTS_K_PLANE_TRACE);
         }
         return OOTS_OK;

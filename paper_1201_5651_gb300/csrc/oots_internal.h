@@ -23,16 +23,15 @@ struct Job {
 };
 
 // One plane-parallel source of one grid (a source at infinity whose rays run
-// along a grid axis, Sect. 3.1): its rows are traced independently.  Rows of
-// axis 0 take one warp each (a warp scan along the contiguous row); rows of
-// axes 1 and 2 one thread each (neighbouring threads hold neighbouring x).
+// along a grid axis, Sect. 3.1): its rows are traced independently (the
+// thread layout per axis is in plane.cu).
 struct PlaneJob {
     int grid;              // index into the launch's grid array
     int src;               // source index within the grid
     int code;              // 2*axis + back: rays along +axis (back 0) or -axis (back 1)
     int pad;
     long long rows;        // rows of cells parallel to the axis
-    long long first;       // first thread of the job in the launch (a multiple of 32)
+    long long first;       // first thread of the job in the launch (a multiple of 256)
 };
 
 // One tile of a job, ordered in the work list by tile diagonal I+J+K.

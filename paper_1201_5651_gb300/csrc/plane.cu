@@ -13,10 +13,12 @@
 // row loses in it over the cell volume per unit face area, dx (src_rate with
 // plane = true).
 //
-// Row layout (x fastest): rows of axis 0 are contiguous and take one warp each
-// (a warp scan over 32 cells at a time); rows of axes 1 and 2 take one thread
-// each, numbered so that neighbouring threads hold neighbouring x and every
-// load of a warp is one coalesced line.
+// Row layout (x fastest): rows of axis 0 are contiguous and take one warp each;
+// rows of axes 1 and 2 are numbered so that neighbouring rows start at
+// neighbouring x, and a warp's lanes hold 32 of them, so every load of a warp
+// is one coalesced line.  The trace keeps many loads in flight per thread
+// (see the kernel); the A1 row integration is ALU-bound and takes one thread
+// per row.
 #include "common.cuh"
 #include "integrator.cuh"
 #include "kernels.h"
@@ -60,62 +62,161 @@ __device__ __forceinline__ Real cell_n(const GridDev<Real> &G, long long g)
     return G.n ? __ldg(G.n + g) : G.n_uniform;
 }
 
-// Columns of every plane source of the launch: which = 0 traces x into N1,
-// which = 1 traces the half-step state xh into N2.
-template <typename Real>
-__global__ void __launch_bounds__(256) plane_trace_kernel(const GridDev<Real> *grids, const PlaneJob *jobs, int njobs,
-                                                          long long nthreads, int which)
+// Column accumulation without FP64 arithmetic in the mixed path (GB300 runs
+// FP64 at a small fraction of its FP32 rate): the running sum of n x is a
+// float-float (ff) value there and a double in the FP64 path, and dx is
+// applied once per output.  In FP64 each cell costs two fused multiply-adds.
+__device__ __forceinline__ double acc_nx(double pre, double n, double x) { return fma(n, x, pre); }
+__device__ __forceinline__ ff acc_nx(ff pre, float n, float x) { return ff_add_f(pre, n * x); }
+__device__ __forceinline__ double col_out(double base_dx, double pre, double dx) { return fma(pre, dx, base_dx); }
+__device__ __forceinline__ float col_out(ff base, ff pre, float dx) { ff s = ff_add(base, pre); return (s.hi + s.lo) * dx; }
+__device__ __forceinline__ double col_base(double base, double dx) { return base * dx; }
+__device__ __forceinline__ ff col_base(ff base, float) { return base; }
+__device__ __forceinline__ double shfl_up_col(double v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ ff shfl_up_col(ff v, int o)
 {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t - (threadIdx.x & 31) >= nthreads) return;           // whole warps leave together
-    const PlaneJob J = jobs[find_plane_job(jobs, njobs, t - (threadIdx.x & 31))];
+    return ff{__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ double shfl_col(double v, int l) { return __shfl_sync(0xffffffffu, v, l); }
+__device__ __forceinline__ ff shfl_col(ff v, int l)
+{
+    return ff{__shfl_sync(0xffffffffu, v.hi, l), __shfl_sync(0xffffffffu, v.lo, l)};
+}
+
+// Columns of the plane sources of one launch: which = 0 traces x into N1,
+// which = 1 traces the half-step state xh into N2.  Blocks of 256 threads; a
+// block belongs to one job (jobs start on multiples of 256 threads); t_base is
+// the launch's first thread in the jobs' numbering.  In both layouts a thread
+// sums a run of consecutive cells of its row on its own and only the run
+// totals are scanned across threads.
+//   rows along x (ROWX): one warp per row, 256 cells at a time; lane l takes
+//     cells [8l, 8l + 8) of the stretch, the 32 lane totals are scanned by
+//     shuffles;
+//   rows along y or z: a block holds 32 neighbouring rows (lane = row,
+//     neighbouring x, so each warp load is one line) and walks them 256 cells
+//     at a time; warp w takes cells [32w, 32w + 32) of the stretch, the eight
+//     warp totals are scanned through shared memory.  The mixed path keeps the
+//     run's products n x in registers (its loads all issue before the sums);
+//     the FP64 path keeps the run's prefix sums (one fused multiply-add each).
+constexpr int kRun0 = 8;     // cells per lane and stretch, rows along x
+constexpr int kRun1 = 32;    // cells per lane and stretch, rows along y or z
+
+template <typename Real, bool ROWX>
+__global__ void __launch_bounds__(256, ROWX ? 3 : 2) plane_trace_kernel(const GridDev<Real> *grids,
+                                                                        const PlaneJob *jobs, int njobs,
+                                                                        long long t_base, long long t_end, int which)
+{
+    typedef typename ColT<Real>::type Col;
+    const long long t0 = t_base + (long long)blockIdx.x * blockDim.x;   // first thread of the block
+    if (t0 >= t_end) return;                                          // whole blocks leave together
+    const PlaneJob J = jobs[find_plane_job(jobs, njobs, t0)];
     const GridDev<Real> &G = grids[J.grid];
-    const Real *x = which ? G.xh : G.x;
-    Real *Nout = (which ? G.N2 : G.N1) + (long long)J.src * G.ncell;
-    const double dx = double(G.dx);
-    if ((J.code >> 1) == 0) {
-        // one warp per row: exclusive warp scans, 32 cells at a time
-        const long long r = (t - J.first) >> 5;
-        if (r >= J.rows) return;                                 // uniform over the warp
-        const int lane = threadIdx.x & 31;
+    const Real *__restrict__ x = which ? G.xh : G.x;
+    // loads without branches, so that a run's loads all issue before its sums:
+    // a uniform density is read through a zero stride from the grid record,
+    // and cells past the row end read the row's first cell and count zero
+    const Real *__restrict__ nd = G.n ? G.n : &grids[J.grid].n_uniform;
+    const long long nmul = G.n ? 1 : 0;
+    Real *__restrict__ Nout = (which ? G.N2 : G.N1) + (long long)J.src * G.ncell;
+    const Real dx = G.dx;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (ROWX) {
+        const long long r = (t0 - J.first + threadIdx.x) >> 5;
+        if (r >= J.rows) return;                                   // uniform over the warp
         const PlaneRow R = plane_row(G, J.code, r);
-        double carry = 0.0;
-        for (int m0 = 0; m0 < R.len; m0 += 32) {
-            const int m = m0 + lane;
-            const long long g = R.base + (long long)m * R.step;
-            double dN = 0.0;
-            if (m < R.len) dN = double(cell_n(G, g)) * double(x[g]) * dx;
-            double inc = dN;
+        Col carry = ColT<Real>::zero();
+        for (int m0 = 0; m0 < R.len; m0 += 32 * kRun0) {
+            const int mb = m0 + kRun0 * lane;
+            Real nn[kRun0], xx[kRun0];
+#pragma unroll
+            for (int q = 0; q < kRun0; q++) {
+                const int m = mb + q;
+                const long long g = R.base + (long long)(m < R.len ? m : 0) * R.step;
+                const Real xv = __ldg(x + g);
+                nn[q] = __ldg(nd + g * nmul);
+                xx[q] = m < R.len ? xv : Real(0);
+            }
+            Col pre[kRun0 + 1];
+            pre[0] = ColT<Real>::zero();
+#pragma unroll
+            for (int q = 0; q < kRun0; q++) pre[q + 1] = acc_nx(pre[q], nn[q], xx[q]);
+            // exclusive scan of the lane totals
+            Col inc = pre[kRun0];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const double v = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += v;
+                const Col v = shfl_up_col(inc, o);
+                if (lane >= o) inc = ColT<Real>::addc(inc, v);
             }
-            double exc = __shfl_up_sync(0xffffffffu, inc, 1);
-            if (lane == 0) exc = 0.0;
-            if (m < R.len) Nout[g] = Real(carry + exc);
-            carry += __shfl_sync(0xffffffffu, inc, 31);
+            Col exc = shfl_up_col(inc, 1);
+            if (lane == 0) exc = ColT<Real>::zero();
+            const auto base = col_base(ColT<Real>::addc(carry, exc), dx);
+#pragma unroll
+            for (int q = 0; q < kRun0; q++) {
+                const int m = mb + q;
+                if (m < R.len) Nout[R.base + (long long)m * R.step] = Real(col_out(base, pre[q], dx));
+            }
+            carry = ColT<Real>::addc(carry, shfl_col(inc, 31));
         }
         return;
     }
-    // one thread per row; loads of a block of cells are issued before the stores
-    const long long r = t - J.first;
-    if (r >= J.rows) return;
-    const PlaneRow R = plane_row(G, J.code, r);
-    constexpr int B = 8;
-    double N = 0.0;
-    for (int m0 = 0; m0 < R.len; m0 += B) {
-        double dN[B];
+    __shared__ Col s_sum[8][33];
+    __shared__ Col s_carry[32];
+    const long long r = ((t0 - J.first) >> 3) + lane;              // 256 threads per 32 rows
+    const bool live = r < J.rows;
+    const PlaneRow R = plane_row(G, J.code, live ? r : 0);
+    if (warp == 0) s_carry[lane] = ColT<Real>::zero();
+    for (int m0 = 0; m0 < R.len; m0 += 8 * kRun1) {
+        const int mb = m0 + kRun1 * warp;
+        if (sizeof(Real) == 4) {
+            Real nxp[kRun1];
 #pragma unroll
-        for (int q = 0; q < B; q++) {
-            const long long g = R.base + (long long)(m0 + q) * R.step;
-            dN[q] = (m0 + q < R.len) ? double(cell_n(G, g)) * double(x[g]) * dx : 0.0;
-        }
+            for (int q = 0; q < kRun1; q++) {
+                const int m = mb + q;
+                const bool in = live && m < R.len;
+                const long long g = R.base + (long long)(in ? m : 0) * R.step;
+                const Real xv = __ldg(x + g), nv = __ldg(nd + g * nmul);
+                nxp[q] = in ? nv * xv : Real(0);
+            }
+            Col tot = ColT<Real>::zero();
 #pragma unroll
-        for (int q = 0; q < B; q++) {
-            if (m0 + q < R.len) Nout[R.base + (long long)(m0 + q) * R.step] = Real(N);
-            N += dN[q];
+            for (int q = 0; q < kRun1; q++) tot = ColT<Real>::add(tot, nxp[q]);
+            s_sum[warp][lane] = tot;
+            __syncthreads();
+            Col run = s_carry[lane];
+            for (int w = 0; w < warp; w++) run = ColT<Real>::addc(run, s_sum[w][lane]);
+#pragma unroll
+            for (int q = 0; q < kRun1; q++) {
+                const int m = mb + q;
+                if (live && m < R.len) Nout[R.base + (long long)m * R.step] = Real(ColT<Real>::to_real(run) * dx);
+                run = ColT<Real>::add(run, nxp[q]);
+            }
+            __syncthreads();
+            if (warp == 7) s_carry[lane] = run;                    // the stretch's end
+        } else {
+            Col pre[kRun1 + 1];
+            pre[0] = ColT<Real>::zero();
+#pragma unroll
+            for (int q = 0; q < kRun1; q++) {
+                const int m = mb + q;
+                const bool in = live && m < R.len;
+                const long long g = R.base + (long long)(in ? m : 0) * R.step;
+                const Real xv = __ldg(x + g), nv = __ldg(nd + g * nmul);
+                pre[q + 1] = acc_nx(pre[q], nv, in ? xv : Real(0));
+            }
+            s_sum[warp][lane] = pre[kRun1];
+            __syncthreads();
+            Col off = s_carry[lane];
+            for (int w = 0; w < warp; w++) off = ColT<Real>::addc(off, s_sum[w][lane]);
+            const auto base = col_base(off, dx);
+#pragma unroll
+            for (int q = 0; q < kRun1; q++) {
+                const int m = mb + q;
+                if (live && m < R.len) Nout[R.base + (long long)m * R.step] = Real(col_out(base, pre[q], dx));
+            }
+            __syncthreads();
+            if (warp == 7) s_carry[lane] = ColT<Real>::addc(off, pre[kRun1]);
         }
+        __syncthreads();
     }
 }
 
@@ -175,30 +276,36 @@ __global__ void __launch_bounds__(128) plane_implicit_kernel(const GridDev<Real>
 
 long long plane_job_threads(int code, long long rows)
 {
-    const long long t = (code >> 1) == 0 ? rows * 32 : rows;
-    return (t + 31) / 32 * 32;
+    // axis 0: a warp per row; axes 1, 2: 256 threads per 32 rows.  Whole
+    // blocks of 256, so that a block never spans two jobs.
+    const long long t = (code >> 1) == 0 ? rows * 32 : (rows + 31) / 32 * 256;
+    return (t + 255) / 256 * 256;
 }
 
 template <typename Real>
-cudaError_t launch_plane(const GridDev<Real> *grids, const PlaneJob *jobs, int njobs, long long nthreads,
-                         const DevTable<Real> *tabs, int which, int implicit, cudaStream_t s)
+cudaError_t launch_plane(const GridDev<Real> *grids, const PlaneJob *jobs, int njobs, int nrow0, long long nthreads,
+                         long long threads0, const DevTable<Real> *tabs, int which, int implicit, cudaStream_t s)
 {
     if (njobs <= 0 || nthreads <= 0) return cudaSuccess;
     if (implicit) {
         const int bs = 128;
         plane_implicit_kernel<Real><<<(unsigned)((nthreads + bs - 1) / bs), bs, 0, s>>>(grids, jobs, njobs, nthreads,
                                                                                         tabs);
-    } else {
-        const int bs = 256;
-        plane_trace_kernel<Real><<<(unsigned)((nthreads + bs - 1) / bs), bs, 0, s>>>(grids, jobs, njobs, nthreads,
-                                                                                     which);
+        return cudaGetLastError();
     }
+    const int bs = 256;
+    if (nrow0 > 0)
+        plane_trace_kernel<Real, true><<<(unsigned)((threads0 + bs - 1) / bs), bs, 0, s>>>(grids, jobs, nrow0, 0,
+                                                                                          threads0, which);
+    if (njobs > nrow0)
+        plane_trace_kernel<Real, false><<<(unsigned)((nthreads - threads0 + bs - 1) / bs), bs, 0, s>>>(
+            grids, jobs + nrow0, njobs - nrow0, threads0, nthreads, which);
     return cudaGetLastError();
 }
 
-template cudaError_t launch_plane<double>(const GridDev<double> *, const PlaneJob *, int, long long,
+template cudaError_t launch_plane<double>(const GridDev<double> *, const PlaneJob *, int, int, long long, long long,
                                           const DevTable<double> *, int, int, cudaStream_t);
-template cudaError_t launch_plane<float>(const GridDev<float> *, const PlaneJob *, int, long long,
+template cudaError_t launch_plane<float>(const GridDev<float> *, const PlaneJob *, int, int, long long, long long,
                                          const DevTable<float> *, int, int, cudaStream_t);
 
 } // namespace oots

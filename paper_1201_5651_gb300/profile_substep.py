@@ -18,6 +18,11 @@ WORKLOADS = {
     "lognormal128_bb": lambda: inputs.lognormal_bb(128, 1.0, 1202, Q=1e48, T=4e4, box_rs=2.5),
     "lognormal64_bb": lambda: inputs.lognormal_bb(64, 1.0, 1202, Q=1e48, T=4e4, box_rs=2.5),
     "stromgren32": lambda: inputs.stromgren_corner(32),
+    # plane-parallel blackbody source along each axis (rows along x: one warp
+    # per row; along y or z: one thread per row)
+    "plane256_x": lambda: inputs.plane_random(n=256, seed=31, axis=0, spectrum="bb", F=1e10, x_lo=0.9),
+    "plane256_y": lambda: inputs.plane_random(n=256, seed=31, axis=1, spectrum="bb", F=1e10, x_lo=0.9),
+    "plane256_z": lambda: inputs.plane_random(n=256, seed=31, axis=2, spectrum="bb", F=1e10, x_lo=0.9),
 }
 
 
@@ -26,7 +31,7 @@ def main(argv=None):
     ap.add_argument("--workload", default="lognormal128_bb", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--shape", type=int, default=-1, help="tile shape id (-1: library default)")
-    ap.add_argument("--t0", type=float, default=0.05, help="start time in units of t_rec")
+    ap.add_argument("--t0", type=float, default=0.05, help="start time in units of t_rec (0: start at once)")
     args = ap.parse_args(argv)
 
     import torch
@@ -34,7 +39,8 @@ def main(argv=None):
     c = oots.Context.from_workload(w, args.precision, scheme=oots.OOTS_A3, K4=0.25)
     if args.shape >= 0:
         c.set_tile_shape(args.shape)
-    c.advance(args.t0 * w.t_rec)
+    if args.t0 > 0:
+        c.advance(args.t0 * w.t_rec)
     c.profile_substep()                       # build and warm up every launch
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStart()
