@@ -16,7 +16,9 @@ Workloads (sizes, distributions and seeds):
   * ``multisource``: lognormal density with many blackbody sources;
   * ``planar_slab``: the plane-parallel slab of Sect. 3.1 (source at infinity,
     uniform hydrogen, no recombinations);
-  * ``plane_random``: small random grid lit by a plane-parallel source.
+  * ``plane_random``: small random grid lit by a plane-parallel source;
+  * ``stromgren_bb``: uniform gas and a blackbody source at the corner vertex,
+    at a chosen cell optical depth (the multi-frequency test of Sect. 4).
 """
 from __future__ import annotations
 
@@ -251,4 +253,21 @@ def plane_random(n: int = 12, seed: int = 11, axis: int = 0, back: int = 0, F: f
         srcs.append(Source(pos, point_Q, spectrum, T if spectrum == "bb" else 0.0))
     w = Workload("plane_random", n, ny, nz, dtau / (SIGMA0 * 100.0), nH, x0, srcs)
     w.t_rec = 1.0 / (ALPHA_B * 100.0)
+    return w
+
+
+def stromgren_bb(dtau0: float, tau_s: float = 240.0, n_H: float = 10.0, T: float = 37500.0,
+                 box: float = 1.1) -> Workload:
+    """Multi-frequency Stromgren test (Sect. 4) in 3D: uniform hydrogen n_H, a
+    blackbody source at the corner vertex, cell optical depth dtau0 at nu0 and
+    x = 1.  The source rate is set so that the Stromgren radius is tau_s
+    optical depths at nu0 (R_S = tau_s / (sigma0 n_H)); the box side is box R_S,
+    so the grid has ceil(box tau_s / dtau0) cells per side."""
+    R_S = tau_s / (SIGMA0 * n_H)
+    Q = 4.0 * math.pi / 3.0 * ALPHA_B * n_H ** 2 * R_S ** 3
+    dx = dtau0 / (SIGMA0 * n_H)
+    n = int(math.ceil(box * tau_s / dtau0))
+    w = Workload(f"stromgren_bb_dtau{dtau0:g}", n, n, n, dx, _uniform(n, n_H), _uniform(n, X_NEUTRAL),
+                 [Source((0.0, 0.0, 0.0), Q, "bb", T)], uniform_n=n_H)
+    w.t_rec = 1.0 / (ALPHA_B * n_H)
     return w
