@@ -47,6 +47,24 @@ __device__ __forceinline__ int cell_rates(const GridDev<Real> &G, const Real *Nc
     return G.nsrc;
 }
 
+// Mixed path: warp sums of two FP32 values, scaled to FP64 once per warp,
+// then the block sum in FP64; thread 0 gets both (one pair of barriers).
+__device__ __forceinline__ void block_sum2_f(float a, float b, double scale, double &ra, double &rb, double *sh)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) { sh[2 * wid] = double(a) * scale; sh[2 * wid + 1] = double(b) * scale; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ra = 0.0; rb = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) { ra += sh[2 * w]; rb += sh[2 * w + 1]; }
+    }
+}
+
 // Block sums of two values in one pass (one pair of barriers); thread 0 gets both.
 __device__ __forceinline__ void block_sum2(double &a, double &b, double *sh)
 {
@@ -81,15 +99,33 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
         s_grid_hi = find_grid(offsets, ngrid, last);
     }
     __syncthreads();
+    // mixed path: the step and the Eq. 4 factors in FP32, converted once per
+    // block (this GPU runs FP64 at a small fraction of its FP32 rate, so the
+    // per-cell criterion and budget stay off the FP64 pipe)
+    constexpr bool F32 = sizeof(Real) == 4;
+    __shared__ float s_f[4];
     for (int gi = s_grid_lo; gi <= s_grid_hi; gi++) {
         const GridDev<Real> &G = grids[gi];
         DevState *st = G.st;
         const long long idx = base + threadIdx.x;
         const bool mine = idx < total && idx >= offsets[gi] && (gi + 1 >= ngrid || idx < offsets[gi + 1]);
-        const double dtd = st->dt;
-        const bool active = mine && (OP == OP_RATEDT || dtd > 0.0) && !(OP == OP_RATEDT && st->done);
+        if (F32) {
+            if (threadIdx.x == 0) {
+                const double d = st->dt;
+                s_f[0] = float(OP == OP_HALF ? 0.5 * d : d);
+                s_f[1] = float(st->K1);
+                s_f[2] = float(st->K3);
+                s_f[3] = float(st->K4);
+            }
+            __syncthreads();
+        }
+        const double dtd = F32 ? 0.0 : st->dt;
+        const bool stepping = F32 ? s_f[0] > 0.0f : dtd > 0.0;
+        const bool active = mine && (OP == OP_RATEDT || stepping) && !(OP == OP_RATEDT && st->done);
         double dtmin = __longlong_as_double(0x7ff0000000000000ll);
+        float dtmin_f = __int_as_float(0x7f800000);
         double ions = 0.0, rec = 0.0;
+        float ions_f = 0.0f, rec_f = 0.0f;
         bool defer = false;
         Real rv[QREC];
         if (active) {
@@ -115,31 +151,46 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
                 // Eq. 4 with T fixed: K1 t_rec, K3 max(0.05, x)/|dx/dt|, K4/|dx/dt|
                 Real F, dF;
                 ode_F<Real, NSMAX>(C, x0, &F, &dF);
-                const double xd = fabs((double)(-F + C.c * (Real(1) - x0) * (Real(1) - x0)));
                 if (NSMAX == 1 && rcache && C.ns > 0) {
                     rcache[idx] = r[0].p;
                     rcache[total + idx] = F;
                     rcache[2 * total + idx] = dF;
                 }
-                if (st->K1 > 0) dtmin = fmin(dtmin, st->K1 / (double(G.alpha) * double(n)));
-                if (xd > 0) {
-                    if (st->K3 > 0) dtmin = fmin(dtmin, st->K3 * fmax(0.05, (double)x0) / xd);
-                    if (st->K4 > 0) dtmin = fmin(dtmin, st->K4 / xd);
+                if (F32) {
+                    const float xd = fabsf(float(-F + C.c * (Real(1) - x0) * (Real(1) - x0)));
+                    if (s_f[1] > 0.0f) dtmin_f = fminf(dtmin_f, s_f[1] / (float(G.alpha) * float(n)));
+                    if (xd > 0.0f) {
+                        if (s_f[2] > 0.0f) dtmin_f = fminf(dtmin_f, s_f[2] * fmaxf(0.05f, float(x0)) / xd);
+                        if (s_f[3] > 0.0f) dtmin_f = fminf(dtmin_f, s_f[3] / xd);
+                    }
+                } else {
+                    const double xd = fabs((double)(-F + C.c * (Real(1) - x0) * (Real(1) - x0)));
+                    if (st->K1 > 0) dtmin = fmin(dtmin, st->K1 / (double(G.alpha) * double(n)));
+                    if (xd > 0) {
+                        if (st->K3 > 0) dtmin = fmin(dtmin, st->K3 * fmax(0.05, (double)x0) / xd);
+                        if (st->K4 > 0) dtmin = fmin(dtmin, st->K4 / xd);
+                    }
                 }
             } else {
                 // closed forms here; the rest goes to the warp-per-cell pass
                 IntResult<Real> R;
                 Real F0 = Real(0), dF0 = Real(0), f0;
-                const Real h = Real(OP == OP_HALF ? 0.5 * dtd : dtd);
+                const Real h = F32 ? Real(s_f[0]) : Real(OP == OP_HALF ? 0.5 * dtd : dtd);
                 if (cached && C.ns > 0) { F0 = rcache[total + idx]; dF0 = rcache[2 * total + idx]; }
                 if (integrate_prelude<Real, NSMAX>(C, x0, h, G.sigma0, R, F0, dF0, f0, cached && C.ns > 0)) {
                     if (OP == OP_HALF) {
                         const_cast<Real *>(G.xh)[g] = R.x;
                     } else {
                         G.xout[g] = R.x;
-                        const double nV = double(n) * st->cell_volume;
-                        ions = nV * (double(x0) - double(R.x));
-                        rec = nV * double(R.IR);
+                        if (F32) {
+                            // per H atom times n; the cell volume is applied per warp
+                            ions_f = float(n) * (float(x0) - float(R.x));
+                            rec_f = float(n) * float(R.IR);
+                        } else {
+                            const double nV = double(n) * st->cell_volume;
+                            ions = nV * (double(x0) - double(R.x));
+                            rec = nV * double(R.IR);
+                        }
                     }
                 } else {
                     defer = true;
@@ -169,7 +220,12 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
             }
         }
         if (OP == OP_RATEDT) {
-            for (int o = 16; o > 0; o >>= 1) dtmin = fmin(dtmin, __shfl_down_sync(0xffffffffu, dtmin, o));
+            if (F32) {
+                for (int o = 16; o > 0; o >>= 1) dtmin_f = fminf(dtmin_f, __shfl_down_sync(0xffffffffu, dtmin_f, o));
+                if ((threadIdx.x & 31) == 0) dtmin = double(dtmin_f);   // lane 0 carries the warp minimum
+            } else {
+                for (int o = 16; o > 0; o >>= 1) dtmin = fmin(dtmin, __shfl_down_sync(0xffffffffu, dtmin, o));
+            }
             const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
             __syncthreads();
             if (lane == 0) sh[wid] = dtmin;
@@ -181,7 +237,8 @@ __global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, i
             }
         } else if (OP == OP_FULL1 || OP == OP_FULL2) {
             double si = ions, sr = rec;
-            block_sum2(si, sr, sh);
+            if (F32) block_sum2_f(ions_f, rec_f, st->cell_volume, si, sr, sh);
+            else block_sum2(si, sr, sh);
             if (threadIdx.x == 0 && (si != 0.0 || sr != 0.0)) {
                 atomicAdd(&st->bud_step[1], si + sr);   // absorbed = new ions + recombinations
                 atomicAdd(&st->bud_step[2], si);

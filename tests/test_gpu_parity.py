@@ -220,3 +220,20 @@ def test_argument_errors():
     with pytest.raises(oots.OotsError) as e:
         c.step(1e6)
     assert e.value.code == oots.OOTS_E_UNSUPPORTED
+
+
+def test_mixed_budget_and_dt_against_fp64():
+    """The mixed path forms the Eq. 4 criterion and the photon budget in FP32
+    (warp sums scaled to FP64): dt within 1e-5 and every budget term within
+    1e-4 of the absorbed total, against the FP64 path on the same state."""
+    w = inputs.small_random(n=24, ny=20, nz=22, seed=77, nsrc=1, spectrum="bb", x_lo=0.5)
+    cm = _ctx(w, "mixed", scheme=3, K4=0.25)
+    cf = _ctx(w, "fp64", scheme=3, K4=0.25)
+    dm, df = cm.compute_dt(), cf.compute_dt()
+    assert abs(dm / df - 1) <= 1e-5, (dm, df)
+    for c in (cm, cf):
+        c.step(df)
+    bm, bf = cm.get_budget(), cf.get_budget()
+    assert abs(bm[0] / bf[0] - 1) <= 1e-6
+    for q in (1, 2, 3):
+        assert abs(bm[q] - bf[q]) <= 1e-4 * abs(bf[1]), (q, bm, bf)
