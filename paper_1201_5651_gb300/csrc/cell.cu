@@ -83,7 +83,7 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *sh)
 }
 
 template <typename Real, int OP, int NSMAX>
-__global__ void __launch_bounds__(256) cell_kernel(const GridDev<Real> *grids, int ngrid, const long long *offsets,
+__global__ void __launch_bounds__(256, 4) cell_kernel(const GridDev<Real> *grids, int ngrid, const long long *offsets,
                                                    long long total, const DevTable<Real> *tabs, unsigned *queue,
                                                    unsigned *qcount, Real *qrec, Real *rcache, int use_cache)
 {
