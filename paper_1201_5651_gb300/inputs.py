@@ -84,7 +84,7 @@ def gaussian_random_field(n: int, seed: int, slope: float = -3.0) -> np.ndarray:
     k2[0, 0, 0] = 1.0
     amp = k2 ** (slope / 4.0)          # sqrt(P) = k^(slope/2)
     amp[0, 0, 0] = 0.0
-    g = np.fft.irfftn(fk * amp, s=(n, n, n))
+    g = np.fft.irfftn(fk * amp, s=(n, n, n), axes=(0, 1, 2))
     g -= g.mean()
     g /= g.std()
     return g
