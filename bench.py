@@ -346,6 +346,8 @@ def run_ours(args, rank, world, local_rank):
                    "tile_shape": {k: oots.oots_tile_shape_info(v)[1] if v is not None else None for k, v in tuned.items()}},
         "fp64": {"value": value_fp64, "ms_per_step": t_fp64 / k64, "steps": k64},
         "mixed_over_fp64": value / value_fp64,
+        # an A3 substep traces every cell twice: cell-sweeps/s compares A3 with A2 (one trace per substep)
+        "cell_sweeps_per_s": 2.0 * value,
         "accuracy_vs_fp64": acc,
         "roofline": {"bound": "hbm", "kernel": dom + (" (closed-form + general pass)" if dom in ("half", "full") else ""),
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
