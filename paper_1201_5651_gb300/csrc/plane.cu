@@ -3,8 +3,9 @@
 // short-characteristics interpolation reduces to the one upwind cell on the
 // same row, so the column to the entry of a cell is the sum of n x dx over the
 // cells before it on its row and every row is independent:
-//   - trace: an exclusive prefix sum of n x dx along each row (FP64 sums in
-//     both precisions), written to the source's column array;
+//   - trace: an exclusive prefix sum of n x dx along each row (float-float
+//     sums in the mixed path, double in the FP64 path), written to the
+//     source's column array;
 //   - implicit (A1, Sect. 2.1, Eq. 3): along each row, in the direction of
 //     travel, every cell is integrated over dt with its entry column frozen and
 //     hands downstream N_out = N_in - ln<f>/sigma0 from its time-averaged
