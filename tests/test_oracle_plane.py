@@ -155,3 +155,22 @@ def test_rates_of_plane_and_point_sources_add():
         parts.append(Ps.rates(x, N[s:s + 1])[0])
     assert np.max(np.abs(F - parts[0] - parts[1]) / np.maximum(F, 1e-300)) < 1e-13
     assert np.all(parts[0] > 0) and np.all(parts[1] > 0)
+
+
+def test_tabulated_plane_source_with_delta_spectrum_equals_monochromatic():
+    """A plane source with a tabulated delta spectrum (all photons at nu0) gives
+    the same columns and the same A3 substeps as the monochromatic plane source:
+    pins the tabulated rate of a plane source against the exponential one."""
+    w = inputs.plane_random(n=7, ny=6, nz=5, seed=8, axis=1, back=0, F=3e10)
+    Pm = oracle.Problem.from_workload(w)
+    srcs = [(s.pos, s.Q, "tab", 0.0, s.plane) for s in w.sources]
+    Pt = oracle.Problem(w.nx, w.ny, w.nz, w.dx, w.nH, srcs, alpha=w.alpha, sigma0=w.sigma0, tau0=w.tau0,
+                        tables=[oracle.table_build("delta")])
+    a = w.x0.copy()
+    b = w.x0.copy()
+    dt = 0.02 * w.t_rec
+    for _ in range(2):
+        Pm.substep(a, 0.0, dt, scheme=3, dt_fixed=dt)
+        Pt.substep(b, 0.0, dt, scheme=3, dt_fixed=dt)
+    assert np.max(np.abs(a - b)) <= 1e-9
+    assert np.max(np.abs(a - w.x0)) > 1e-3
