@@ -174,3 +174,24 @@ def test_tabulated_plane_source_with_delta_spectrum_equals_monochromatic():
         Pt.substep(b, 0.0, dt, scheme=3, dt_fixed=dt)
     assert np.max(np.abs(a - b)) <= 1e-9
     assert np.max(np.abs(a - w.x0)) > 1e-3
+
+
+def test_a1_and_a3_converge_together_with_recombinations():
+    """With recombinations on, the implicit row sweep (A1, fixed small steps)
+    and the explicit scheme (A3, tight K4) are different algorithms for the same
+    equations; at small steps both converge to one solution.  A front in an
+    optically thick slab (cell dtau 5), six crossing times."""
+    w = inputs.plane_random(n=16, ny=3, nz=2, seed=12, axis=0, back=0, F=1e9, x_lo=1 - 1e-6, dtau=5.0,
+                            sigma_ln=0.3)
+    P = oracle.Problem.from_workload(w)
+    T = 6 * 100.0 * w.dx / 1e9
+    a1 = w.x0.copy()
+    P.run(a1, 0.0, T, scheme=1, dt_fixed=T / 400)
+    a3 = w.x0.copy()
+    P.run(a3, 0.0, T, scheme=3, K4=1 / 64)
+    coarse = w.x0.copy()
+    P.run(coarse, 0.0, T, scheme=3, K4=1 / 4)
+    assert float((1 - a3).sum()) > 20                      # the front has moved several cells in
+    assert np.max(np.abs(a1 - a3)) <= 5e-4
+    assert abs(float((1 - a1).sum()) / float((1 - a3).sum()) - 1) <= 1e-4
+    assert np.max(np.abs(coarse - a3)) > 10 * np.max(np.abs(a1 - a3))   # the agreement is not trivial
