@@ -1,0 +1,58 @@
+// Host build of the library's cell integrator (the same __host__ __device__
+// code the CUDA kernels run), for CPU tests against the oracle.  Test
+// infrastructure: compiled by tests/test_integrator_host.py, never linked into
+// the library.
+#include "../../paper_1201_5651_gb300/csrc/common.cuh"
+#include "../../paper_1201_5651_gb300/csrc/integrator.cuh"
+#include <cmath>
+
+using namespace oots;
+
+template <typename Real>
+static void integrate_mono(double A, double b, double Nin, double c, double b0, double sigma0, double x0, double h,
+                           double *out)
+{
+    SrcRate<Real> r;
+    r.A = Real(A); r.b = Real(b); r.Nin = Real(Nin); r.p = Real(1); r.tab = -1;
+    CellODE<Real> C;
+    C.ns = 1; C.c = Real(c); C.b0 = Real(b0); C.r = &r; C.tabs = nullptr;
+    const IntResult<Real> R = integrate_cell<Real, 1>(C, Real(x0), Real(h), Real(sigma0));
+    out[0] = double(R.x);
+    out[1] = double(R.IR);
+    out[2] = double(R.lnfav);
+}
+
+// One monochromatic cell: F(x) = A (1 - exp(-b x)), dx/dt = -F + c (1 - x)^2,
+// over h from x0; b0 > 0 also averages exp(-b0 x) (A1).  out: x(h), the
+// recombinations per atom, ln <exp(-b0 x)>.  precision 0: double, 1: float.
+extern "C" void oots_host_integrate_mono(int precision, double A, double b, double Nin, double c, double b0,
+                                         double sigma0, double x0, double h, double *out)
+{
+    if (precision == 0) integrate_mono<double>(A, b, Nin, c, b0, sigma0, x0, h, out);
+    else integrate_mono<float>(A, b, Nin, c, b0, sigma0, x0, h, out);
+}
+
+// A1 along one row lit by a plane-parallel monochromatic flux F, as the row
+// kernel runs it: each cell integrates over dt with its entry column frozen and
+// passes N_out = N_in - ln<f>/sigma0 on.  n, x (in/out) hold ncell values;
+// returns the photons the row absorbed per unit area over nsteps steps.
+extern "C" double oots_host_a1_row(int precision, int ncell, double F, double sigma0, double alpha, double dx,
+                                   const double *n, double *x, double dt, int nsteps)
+{
+    double ions = 0.0;
+    for (int s = 0; s < nsteps; s++) {
+        double N = 0.0;
+        for (int m = 0; m < ncell; m++) {
+            const double A = F * std::exp(-sigma0 * N) / (n[m] * dx);
+            double out[3];
+            oots_host_integrate_mono(precision, A, sigma0 * n[m] * dx, N, alpha * n[m], sigma0 * n[m] * dx, sigma0,
+                                     x[m], dt, out);
+            double dtau = -out[2];
+            if (!(dtau >= 0.0)) dtau = 0.0;
+            ions += n[m] * dx * (x[m] - out[0]);
+            x[m] = out[0];
+            N += dtau / sigma0;
+        }
+    }
+    return ions;
+}

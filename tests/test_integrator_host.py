@@ -1,0 +1,90 @@
+"""The library's cell integrator (the __host__ __device__ code of
+integrator.cuh) built for the host with nvcc and checked on the CPU against
+the oracle and against photon conservation.  This runs the product's
+arithmetic without a GPU; the GPU tests check the kernels around it.
+
+- Single monochromatic cells over the regimes of Eq. 2 (thin, opaque, stiff,
+  near equilibrium, recombination-dominated, no recombinations): x(h) against
+  the oracle's integration, FP64 to 1e-10 and FP32 to 1e-4.
+- A1 on a row lit by a plane-parallel flux with no recombinations (Sect. 3.1):
+  ions per unit area = F t; FP64 to 1e-11, FP32 to 1e-5.  A subnormal rate
+  deep in the row once moved x by 1% here.
+"""
+import ctypes
+import os
+import platform
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "host", "integrator_host.cu")
+SIG, ALPHA = 6.3e-18, 2.59e-13
+
+
+@pytest.fixture(scope="module")
+def lib():
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    out = os.path.join(HERE, "host", f"_libintegrator_host_{platform.machine()}.so")
+    deps = [SRC] + [os.path.join(HERE, "..", "paper_1201_5651_gb300", "csrc", f)
+                    for f in ("common.cuh", "integrator.cuh", "oots_internal.h")]
+    if not os.path.exists(out) or os.path.getmtime(out) < max(os.path.getmtime(d) for d in deps):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call([nvcc, "-std=c++17", "-O2", "-x", "cu", "-shared", "-Xcompiler", "-fPIC",
+                               "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp, SRC])
+        os.replace(tmp, out)
+    L = ctypes.CDLL(out)
+    d = ctypes.c_double
+    L.oots_host_integrate_mono.argtypes = [ctypes.c_int, d, d, d, d, d, d, d, d, ctypes.c_void_p]
+    L.oots_host_integrate_mono.restype = None
+    L.oots_host_a1_row.argtypes = [ctypes.c_int, ctypes.c_int, d, d, d, d, ctypes.c_void_p, ctypes.c_void_p, d,
+                                   ctypes.c_int]
+    L.oots_host_a1_row.restype = d
+    return L
+
+
+def _cell(L, precision, A, b, c, x0, h, b0=0.0):
+    out = np.zeros(3)
+    L.oots_host_integrate_mono(precision, A, b, 0.0, c, b0, SIG, x0, h, out.ctypes.data)
+    return out
+
+
+CASES = [  # (A [1/s], b, c [1/s], x0, h [s])
+    (1e-9, 0.05, ALPHA * 100, 1 - 1e-6, 3e8),      # optically thin, slow
+    (1e-8, 300.0, ALPHA * 100, 1 - 1e-6, 1e9),     # opaque front cell
+    (1e-6, 10.0, ALPHA * 100, 0.9, 1e9),           # stiff
+    (3e-10, 2.0, ALPHA * 100, 0.02, 5e9),          # near equilibrium
+    (1e-14, 5.0, ALPHA * 1000, 0.3, 2e9),          # recombination-dominated
+    (2e-9, 8.0, 0.0, 1 - 1e-6, 4e8),               # no recombinations
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_host_integrator_matches_oracle(lib, case):
+    A, b, c, x0, h = case
+    xo, IF, IR, _ = oracle.integrate(x0, h, c, [(0, A, b, 0.0)])
+    for precision, tol in ((0, 1e-10), (1, 1e-4)):
+        x, ir, _ = _cell(lib, precision, A, b, c, x0, h)
+        assert abs(x - xo) <= tol, (precision, x, xo)
+        assert abs(ir - IR) <= tol * max(1.0, abs(IR)) + 1e-12, (precision, ir, IR)
+
+
+def test_host_a1_row_conserves_photons(lib):
+    n_cells, F, n, dtau = 100, 1e9, 100.0, 10.0
+    dx = dtau / (SIG * n)
+    tc = n * dx / F
+    dt, steps = 0.7 * tc, 57
+    for precision, tol in ((0, 1e-11), (1, 1e-5)):
+        nn = np.full(n_cells, n)
+        x = np.full(n_cells, 1 - 1e-6)
+        ions = lib.oots_host_a1_row(precision, n_cells, F, SIG, 0.0, dx, nn.ctypes.data, x.ctypes.data, dt, steps)
+        assert abs(ions / (F * dt * steps) - 1) <= tol, (precision, ions / (F * dt * steps) - 1)
+        # the front stands where F t / n puts it, the rest of the row is untouched
+        front = F * dt * steps / (n * dx)
+        assert np.all(x[: int(front) - 2] < 1e-3) and np.all(x[int(front) + 3:] > 1 - 2e-6)
