@@ -56,3 +56,57 @@ extern "C" double oots_host_a1_row(int precision, int ncell, double F, double si
     }
     return ions;
 }
+
+// ---- blackbody tables (tables.cpp builds them on the host, as the library does)
+#include "../../paper_1201_5651_gb300/csrc/tables.h"
+#include <vector>
+
+template <typename Real> struct HostDevTable {
+    std::vector<Real> coef, L, Nn;
+    DevTable<Real> T;
+    explicit HostDevTable(const HostTable &H)
+        : coef(H.coef.begin(), H.coef.end()), L(H.L.begin(), H.L.end()), Nn(H.Nnode.begin(), H.Nnode.end())
+    {
+        T.coef = coef.data(); T.L = L.data(); T.Nnode = Nn.data();
+        T.lnN_lo = Real(H.lnN_lo); T.dl = Real(H.dl); T.inv_dl = Real(1.0 / H.dl);
+        T.N0 = Real(H.Nnode[0]); T.Nhi = Real(H.Nnode[H.K - 1]); T.a0 = Real(H.a0); T.K = H.K;
+    }
+};
+
+// ln(P(N)/Q) of the blackbody table at T (precision 0: double, 1: float)
+extern "C" void oots_host_table_lnp(int precision, double Tbb, double sigma0, const double *N, int m, double *out)
+{
+    const HostTable &H = host_table(1, Tbb, sigma0);
+    if (precision == 0) {
+        HostDevTable<double> D(H);
+        for (int i = 0; i < m; i++) out[i] = tab_lnp(D.T, N[i]);
+    } else {
+        HostDevTable<float> D(H);
+        for (int i = 0; i < m; i++) out[i] = double(tab_lnp(D.T, float(N[i])));
+    }
+}
+
+template <typename Real>
+static void integrate_bb(const HostTable &H, double A, double b, double Nin, double c, double sigma0, double x0,
+                         double h, double *out)
+{
+    HostDevTable<Real> D(H);
+    SrcRate<Real> r;
+    r.A = Real(A); r.b = Real(b); r.Nin = Real(Nin); r.tab = 0;
+    r.p = m_exp(tab_lnp(D.T, Real(Nin)));
+    CellODE<Real> C;
+    C.ns = 1; C.c = Real(c); C.b0 = Real(0); C.r = &r; C.tabs = &D.T;
+    const IntResult<Real> R = integrate_cell<Real, 1>(C, Real(x0), Real(h), Real(sigma0));
+    out[0] = double(R.x);
+    out[1] = double(R.IR);
+}
+
+// One cell lit through the blackbody table: F(x) = A [P(Nin) - P(Nin + b x)]/Q
+// with b = n ds (a column per unit x).  out: x(h), recombinations per atom.
+extern "C" void oots_host_integrate_bb(int precision, double Tbb, double A, double b, double Nin, double c,
+                                       double sigma0, double x0, double h, double *out)
+{
+    const HostTable &H = host_table(1, Tbb, sigma0);
+    if (precision == 0) integrate_bb<double>(H, A, b, Nin, c, sigma0, x0, h, out);
+    else integrate_bb<float>(H, A, b, Nin, c, sigma0, x0, h, out);
+}

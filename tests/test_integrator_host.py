@@ -6,6 +6,9 @@ arithmetic without a GPU; the GPU tests check the kernels around it.
 - Single monochromatic cells over the regimes of Eq. 2 (thin, opaque, stiff,
   near equilibrium, recombination-dominated, no recombinations): x(h) against
   the oracle's integration, FP64 to 1e-10 and FP32 to 1e-4.
+- The blackbody rate table (built by the library's own tables.cpp, read by
+  its interpolation) against the oracle's independently built table, and
+  blackbody cells against the oracle's integration.
 - A1 on a row lit by a plane-parallel flux with no recombinations (Sect. 3.1):
   ions per unit area = F t; FP64 to 1e-11, FP32 to 1e-5.  A subnormal rate
   deep in the row once moved x by 1% here.
@@ -32,12 +35,14 @@ def lib():
     if nvcc is None:
         pytest.skip("nvcc not available")
     out = os.path.join(HERE, "host", f"_libintegrator_host_{platform.machine()}.so")
-    deps = [SRC] + [os.path.join(HERE, "..", "paper_1201_5651_gb300", "csrc", f)
-                    for f in ("common.cuh", "integrator.cuh", "oots_internal.h")]
+    csrc = os.path.join(HERE, "..", "paper_1201_5651_gb300", "csrc")
+    deps = [SRC] + [os.path.join(csrc, f) for f in ("common.cuh", "integrator.cuh", "oots_internal.h", "tables.h",
+                                                    "tables.cpp")]
     if not os.path.exists(out) or os.path.getmtime(out) < max(os.path.getmtime(d) for d in deps):
         tmp = out + f".tmp{os.getpid()}"
         subprocess.check_call([nvcc, "-std=c++17", "-O2", "-x", "cu", "-shared", "-Xcompiler", "-fPIC",
-                               "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp, SRC])
+                               "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp, SRC,
+                               os.path.join(csrc, "tables.cpp")])
         os.replace(tmp, out)
     L = ctypes.CDLL(out)
     d = ctypes.c_double
@@ -46,6 +51,10 @@ def lib():
     L.oots_host_a1_row.argtypes = [ctypes.c_int, ctypes.c_int, d, d, d, d, ctypes.c_void_p, ctypes.c_void_p, d,
                                    ctypes.c_int]
     L.oots_host_a1_row.restype = d
+    L.oots_host_table_lnp.argtypes = [ctypes.c_int, d, d, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    L.oots_host_table_lnp.restype = None
+    L.oots_host_integrate_bb.argtypes = [ctypes.c_int, d, d, d, d, d, d, d, d, ctypes.c_void_p]
+    L.oots_host_integrate_bb.restype = None
     return L
 
 
@@ -88,3 +97,32 @@ def test_host_a1_row_conserves_photons(lib):
         # the front stands where F t / n puts it, the rest of the row is untouched
         front = F * dt * steps / (n * dx)
         assert np.all(x[: int(front) - 2] < 1e-3) and np.all(x[int(front) + 3:] > 1 - 2e-6)
+
+
+def test_host_blackbody_table_matches_oracle(lib):
+    T = 4e4
+    P = oracle.Problem(1, 1, 1, 1e16, 100.0, [((0, 0, 0), 1e48, "bb", T)])
+    N = np.concatenate([[0.0, 1e5], np.logspace(8, 25, 400)])
+    ref = np.array([P.lnp(0, v) for v in N])
+    # ln P to 1e-12 (FP64) or 1e-5 relative (FP32: the interpolation runs in float) where P > e^-60 Q
+    for precision, tol in ((0, 1e-12), (1, 1e-5)):
+        out = np.zeros(N.size)
+        lib.oots_host_table_lnp(precision, T, SIG, N.ctypes.data, N.size, out.ctypes.data)
+        fin = np.isfinite(ref) & (ref > -60)
+        err = np.abs(out[fin] - ref[fin]) / np.maximum(1.0, np.abs(ref[fin]))
+        assert float(err.max()) <= tol, (precision, float(err.max()))
+        assert np.all(out[~np.isfinite(ref)] == -np.inf)
+
+
+@pytest.mark.parametrize("Nin", [0.0, 3e16, 4e17, 2e18])
+def test_host_blackbody_cell_matches_oracle(lib, Nin):
+    T, Q, n, ds = 4e4, 1e48, 100.0, 2e16
+    P = oracle.Problem(1, 1, 1, 1e16, 100.0, [((0, 0, 0), Q, "bb", T)])
+    V = 4 * np.pi * (3e17) ** 2 * ds
+    A = Q / (n * V)
+    for x0, h in [(1 - 1e-6, 2e8), (0.4, 1e9), (0.01, 3e9)]:
+        xo, IF, IR, _ = oracle.integrate(x0, h, ALPHA * n, [(1, A, n * ds, Nin, 0)], problem=P)
+        for precision, tol in ((0, 1e-9), (1, 2e-4)):
+            out = np.zeros(3)
+            lib.oots_host_integrate_bb(precision, T, A, n * ds, Nin, ALPHA * n, SIG, x0, h, out.ctypes.data)
+            assert abs(out[0] - xo) <= tol, (precision, x0, h, out[0], xo)
