@@ -110,3 +110,26 @@ extern "C" void oots_host_integrate_bb(int precision, double Tbb, double A, doub
     if (precision == 0) integrate_bb<double>(H, A, b, Nin, c, sigma0, x0, h, out);
     else integrate_bb<float>(H, A, b, Nin, c, sigma0, x0, h, out);
 }
+
+// ln P(Na + dN) - ln P(Na) of the blackbody table, by the library's stable
+// difference (no cancellation for small dN)
+extern "C" void oots_host_table_dlnp(int precision, double Tbb, double sigma0, const double *Na, const double *dN,
+                                     int m, double *out)
+{
+    const HostTable &H = host_table(1, Tbb, sigma0);
+    if (precision == 0) {
+        HostDevTable<double> D(H);
+        for (int i = 0; i < m; i++) out[i] = tab_dlnp(D.T, Na[i], dN[i]);
+    } else {
+        HostDevTable<float> D(H);
+        for (int i = 0; i < m; i++) out[i] = double(tab_dlnp(D.T, float(Na[i]), float(dN[i])));
+    }
+}
+
+// float-float running sum of m floats (the mixed path's column accumulation)
+extern "C" double oots_host_ff_sum(const float *v, int m)
+{
+    ff s = ff_make(0.0f);
+    for (int i = 0; i < m; i++) s = ff_add_f(s, v[i]);
+    return double(s.hi) + double(s.lo);
+}

@@ -152,3 +152,37 @@ def test_host_integrator_random_cells_match_oracle(lib):
         if b0 > 0:
             worst_f = max(worst_f, abs(lnfav - lnf))
             assert abs(lnfav - lnf) <= 1e-9 * max(1.0, abs(lnf)), (k, A, b, c, x0, h, lnfav, lnf)
+
+
+def test_host_table_difference_matches_oracle(lib):
+    """The stable table difference ln P(Na + dN) - ln P(Na), which carries a
+    cell's absorbed fraction without cancellation, against the oracle's own
+    table difference: from steps 1e-12 of the column up to steps of 1e24."""
+    lib.oots_host_table_dlnp.argtypes = [ctypes.c_int] + [ctypes.c_double] * 2 + [ctypes.c_void_p] * 2 + \
+        [ctypes.c_int, ctypes.c_void_p]
+    T = 4e4
+    P = oracle.Problem(1, 1, 1, 1e16, 100.0, [((0, 0, 0), 1e48, "bb", T)])
+    rng = np.random.default_rng(5)
+    Na = np.concatenate([[0.0, 0.0], 10 ** rng.uniform(8, 23.5, 300)])
+    dN = np.concatenate([[1e10, 1e20], Na[2:] * 10 ** rng.uniform(-12, 1.5, 300)])
+    ref = np.array([P.dlnp(0, a, d) for a, d in zip(Na, dN)])
+    out = np.zeros(Na.size)
+    lib.oots_host_table_dlnp(0, T, SIG, Na.ctypes.data, dN.ctypes.data, Na.size, out.ctypes.data)
+    fin = np.isfinite(ref) & (ref > -60)
+    err = np.abs(out[fin] - ref[fin]) / np.maximum(np.abs(ref[fin]), 1e-300)
+    assert fin.sum() > 250 and float(err.max()) <= 1e-8, float(err.max())
+
+
+def test_host_float_float_column_sum(lib):
+    """The mixed path's float-float column accumulation keeps about 44 bits:
+    a running sum of 10^5 positive float increments spanning six decades,
+    against the exactly rounded sum."""
+    import math
+    lib.oots_host_ff_sum.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    lib.oots_host_ff_sum.restype = ctypes.c_double
+    rng = np.random.default_rng(6)
+    v = (10 ** rng.uniform(14, 20, 100000)).astype(np.float32)
+    exact = math.fsum(float(a) for a in v)
+    got = lib.oots_host_ff_sum(v.ctypes.data, v.size)
+    assert abs(got / exact - 1) <= 1e-12, got / exact - 1
+    assert abs(float(np.cumsum(v, dtype=np.float32)[-1]) / exact - 1) > 1e-6   # a running float sum loses this
