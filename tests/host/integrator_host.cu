@@ -133,3 +133,19 @@ extern "C" double oots_host_ff_sum(const float *v, int m)
     for (int i = 0; i < m; i++) s = ff_add_f(s, v[i]);
     return double(s.hi) + double(s.lo);
 }
+
+// Monochromatic rate per H atom F(x) = A (1 - exp(-b x)) of one source for the
+// cell (X, Y, Z) of an nx x ny x nz grid, from the library's src_rate: a point
+// source at vertex v (Q photons/s) or, with plane = 1, a plane source (Q is
+// then its flux).  N is the cell's entry column.
+extern "C" double oots_host_rate_mono(int plane, const int *v, double Q, double sigma0, double dx, double n, int X,
+                                      int Y, int Z, double N, double x)
+{
+    const int i = X >= v[0] ? X - v[0] : v[0] - 1 - X;
+    const int j = Y >= v[1] ? Y - v[1] : v[1] - 1 - Y;
+    const int k = Z >= v[2] ? Z - v[2] : v[2] - 1 - Z;
+    const double qfac = plane ? Q / dx : Q / (4.0 * M_PI * dx * dx * dx);
+    SrcRate<double> r;
+    src_rate<double>(r, qfac, -1, sigma0, dx, n, plane != 0, i, j, k, N, nullptr);
+    return -r.A * std::expm1(-r.b * x);
+}

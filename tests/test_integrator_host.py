@@ -189,3 +189,28 @@ def test_host_float_float_column_sum(lib):
     got = lib.oots_host_ff_sum(v.ctypes.data, v.size)
     assert abs(got / exact - 1) <= 1e-12, got / exact - 1
     assert abs(float(np.cumsum(v, dtype=np.float32)[-1]) / exact - 1) > 1e-6   # a running float sum loses this
+
+
+def test_host_rate_geometry_matches_oracle(lib):
+    """The library's per-cell rate (src_rate: shell volume 4 pi r^2 ds of a
+    point source, volume per unit face area dx of a plane source) against the
+    oracle's rates on a ragged grid with random density, state and columns."""
+    lib.oots_host_rate_mono.argtypes = [ctypes.c_int, ctypes.c_void_p] + [ctypes.c_double] * 4 + \
+        [ctypes.c_int] * 3 + [ctypes.c_double] * 2
+    lib.oots_host_rate_mono.restype = ctypes.c_double
+    rng = np.random.default_rng(8)
+    nx, ny, nz, dx = 7, 5, 6, 3e16
+    nH = 100 * np.exp(rng.standard_normal((nz, ny, nx)))
+    x = rng.uniform(0, 1, (nz, ny, nx))
+    for src in [((2.0, 3.0, 1.0), 1e48, "mono", 0.0), ((0.0, 0.0, 0.0), 3e10, "mono", 0.0, 3)]:
+        P = oracle.Problem(nx, ny, nz, dx, nH, [src])
+        N = 10 ** rng.uniform(15, 18.5, (1, nz, ny, nx))
+        F, _ = P.rates(x, N)
+        plane = len(src) > 4
+        v = (ctypes.c_int * 3)(*[int(c) for c in src[0]])
+        for Z in range(nz):
+            for Y in range(ny):
+                for X in range(nx):
+                    g = lib.oots_host_rate_mono(int(plane), v, src[1], SIG, dx, nH[Z, Y, X], X, Y, Z, N[0, Z, Y, X],
+                                                x[Z, Y, X])
+                    assert abs(g / F[Z, Y, X] - 1) <= 1e-12, (plane, X, Y, Z, g, F[Z, Y, X])
