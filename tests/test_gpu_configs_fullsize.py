@@ -10,6 +10,8 @@ and the launch configuration the library uses for them.
   plain path sum of n x ds over the cells before it (ds = dx |c| / max(c),
   Sect. 2).  Those columns are checked against the sum written out, for two
   sources in all eight octants; every column is finite and non-negative.
+- The 32^3 Stromgren workload (Sect. 3.2), 4000 A3 substeps: the front follows
+  the closed-form Stromgren expansion.
 """
 import math
 
@@ -77,3 +79,22 @@ def test_512_cube_sixteen_sources_axis_columns_mixed():
                 assert float(rel.max()) <= 1e-5, (s, o, axis, float(rel.max()))
                 checked += len(idx)
         assert checked > 1000
+
+
+def test_stromgren_32_cube_front_follows_the_closed_form():
+    """The 32^3 Stromgren workload at full size (n = 100, Q = 1e48, corner
+    source, box 1.5 R_S, dt = t_rec/1000, Sect. 3.2), A3 on the mixed path: the
+    front radius R_eff = (3 V_ion 8 / 4 pi)^(1/3) follows the closed form
+    R_S (1 - e^{-t/t_rec})^(1/3) within 2% from t_rec to 4 t_rec (the oracle on
+    the same grid gives 1.0046-1.0052)."""
+    w = inputs.stromgren_corner(32)
+    c = oots.Context.from_workload(w, "mixed", scheme=3, dt_fixed=w.t_rec / 1000)
+    R_S = inputs.stromgren_radius(w.sources[0].Q, 100.0)
+    for f in (1.0, 2.0, 3.0, 4.0):
+        t, nsub = c.advance(f * w.t_rec)
+        x = c.get_neutral_fraction()
+        R = (3.0 * float((1.0 - x).sum()) * w.dx ** 3 * 8.0 / (4.0 * math.pi)) ** (1.0 / 3.0)
+        ratio = R / (R_S * (1.0 - math.exp(-t / w.t_rec)) ** (1.0 / 3.0))
+        assert abs(ratio - 1.0) <= 0.02, (f, ratio)
+    # 1000 substeps per t_rec (the last one of each advance may be cut to land on its end time)
+    assert 4000 <= c.get_time()[1] <= 4004
