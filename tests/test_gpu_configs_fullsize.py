@@ -12,6 +12,8 @@ and the launch configuration the library uses for them.
   sources in all eight octants; every column is finite and non-negative.
 - The 32^3 Stromgren workload (Sect. 3.2), 4000 A3 substeps: the front follows
   the closed-form Stromgren expansion.
+- The 256^3 clumpy workload after three A3 substeps: axis columns of the
+  traced state equal the path sums.
 """
 import math
 
@@ -98,3 +100,29 @@ def test_stromgren_32_cube_front_follows_the_closed_form():
         assert abs(ratio - 1.0) <= 0.02, (f, ratio)
     # 1000 substeps per t_rec (the last one of each advance may be cut to land on its end time)
     assert 4000 <= c.get_time()[1] <= 4004
+
+
+def test_256_cube_clumpy_axis_columns_after_substeps():
+    """The 256^3 clumpy workload (lognormal sigma_ln 1.5 times 200 clumps,
+    blackbody source at the centre vertex), mixed path.  After three A3-dt02
+    substeps the state is no longer uniform.  One more dt computation traces
+    that state, and its entry columns along the source's eight octant axes
+    equal the path sums of n x ds over the cells before them."""
+    w = inputs.clumpy(256, spectrum="bb")
+    c = oots.Context.from_workload(w, "mixed", scheme=3, K4=0.25)
+    for _ in range(3):
+        c.step(c.compute_dt())
+    x = c.get_neutral_fraction().reshape(w.nz, w.ny, w.nx)
+    assert float(np.abs(x - w.x0).max()) > 0.1              # the front has formed
+    c.compute_dt()                                          # trace of the current state into the columns
+    N = c.get_column_density(0).reshape(w.nz, w.ny, w.nx)
+    n3 = (w.nx, w.ny, w.nz)
+    v = [min(max(int(math.floor(w.sources[0].pos[q] + 0.5)), 0), n3[q]) for q in range(3)]
+    for o in range(8):
+        sg = [-1 if (o >> q) & 1 else 1 for q in range(3)]
+        ext3 = [n3[q] - v[q] if sg[q] > 0 else v[q] for q in range(3)]
+        for axis in range(3):
+            idx, Nref = _axis_path_sums(w.nH, x, w.dx, v, sg, axis, ext3[axis])
+            Ng = np.array([N[z, y, xx] for (z, y, xx) in idx])
+            rel = np.abs(Ng - Nref) / np.maximum(Nref, 1e14)
+            assert float(rel.max()) <= 1e-5, (o, axis, float(rel.max()))
