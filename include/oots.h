@@ -266,10 +266,11 @@ int oots_debug_set(oots_ctx *ctx, int key, long long value);
 /* ---- allocation-free trace --------------------------------------------------------------- */
 
 /* The column-density trace of one source, for callers that cannot allocate
- * device memory -- code that runs inside a CUDA graph capture, inside a
- * pre-sized memory pool or arena, or in a host process whose allocator must
- * not be re-entered.  No counterpart in the paper: it exposes the library's
- * wavefront sweep on its own.
+ * device memory: code that works inside a pre-sized memory pool or arena
+ * that owns the whole device, or a host process whose allocator must not be
+ * re-entered (a cudaMalloc there can fail, fragment the arena or deadlock).
+ * No counterpart in the paper: it exposes the library's wavefront sweep on
+ * its own.
  *
  * Inputs and outputs are caller-owned device buffers (x-fastest, ncell
  * values each): x_dev the neutral fraction, n_dev the density (NULL: the
@@ -286,10 +287,13 @@ int oots_debug_set(oots_ctx *ctx, int key, long long value);
  * roughly 5 million cells) is rejected with OOTS_E_INVAL, *status_detail
  * (optional) set to the tiles needed and the limit in oots_last_error.
  * The first call on a device sets that device up (looks up the scratch's
- * device address and opts the kernel into its shared memory): make the first
- * call before any stream capture.  All calls share the one scratch array and
- * leave it holding the last call's contents; calls that overlap on the GPU
- * (different streams or threads at the same time) race and must not be made.
+ * device address and opts the kernel into its shared memory); that set-up
+ * is serialised across host threads, and the first call should come before
+ * any stream capture.  All calls share the one scratch array and leave it
+ * holding the last call's contents (the call clears what must start at
+ * zero); calls that overlap on the GPU (different streams or threads at the
+ * same time) race and must not be made.  The call synchronises `stream`
+ * before it returns, to read the sweep's error word.
  * Returns OOTS_OK, OOTS_E_INVAL, OOTS_E_CUDA or OOTS_E_DEVICE_TIMEOUT. */
 int oots_trace_noalloc(int device, int precision, int nx, int ny, int nz, double dx_cm,
                        const void *n_dev, double uniform_n, const void *x_dev, const double pos_cells[3],

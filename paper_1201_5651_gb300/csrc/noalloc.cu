@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 
 #include <cuda_runtime.h>
 
@@ -46,10 +47,22 @@ struct DevSetup {
     int nblocks[2] = {0, 0};   // per precision
 };
 static DevSetup g_setup[64];
+static std::mutex g_setup_mutex;   // first-call set-up of a device, from any host thread
 
 template <typename Real> size_t tile_bytes()
 {
     return sizeof(TileItem) + 3 * kFMAX * face_words<Real>() * sizeof(unsigned long long);
+}
+
+// Byte offset of the per-tile arrays, and the most tiles the scratch holds
+// after them (one item slot is kept spare).
+template <typename Real> size_t tiles_offset()
+{
+    return (kOffGrid + sizeof(GridDev<Real>) + 255) / 256 * 256;
+}
+template <typename Real> long long max_tiles()
+{
+    return (long long)((kScratchBytes - tiles_offset<Real>()) / tile_bytes<Real>()) - 1;
 }
 
 // One block orders the tiles of the (at most 8) octant jobs by tile diagonal:
@@ -122,17 +135,15 @@ int trace_noalloc(DevSetup &S, int nx, int ny, int nz, double dx, const void *n_
         if (d > maxd) maxd = d;
         jobs[njobs++] = J;
     }
-    const size_t per_tile = tile_bytes<Real>();
-    const size_t base = (kOffGrid + sizeof(GridDev<Real>) + 255) / 256 * 256;
-    const long long max_tiles = (long long)((kScratchBytes - base) / per_tile) - 1;
-    if (tiles > max_tiles || maxd + 1 > kMaxDiag)
+    const long long maxt = max_tiles<Real>();
+    if (tiles > maxt || maxd + 1 > kMaxDiag)
         return -1000 - (int)std::min<long long>(tiles, 1 << 30);   // reported by the caller
 
     unsigned char *sc = S.scratch;
     // layout of the per-tile arrays after the fixed part
-    size_t off = base;
+    size_t off = tiles_offset<Real>();
     TileItem *items = (TileItem *)(sc + off);
-    off += (size_t)(max_tiles + 1) * sizeof(TileItem);
+    off += (size_t)(maxt + 1) * sizeof(TileItem);
     off = (off + 255) / 256 * 256;
     unsigned long long *faces = (unsigned long long *)(sc + off);   // zero at load; launches tag epochs 1, 2, ...
 
@@ -209,6 +220,7 @@ extern "C" int oots_trace_noalloc(int device, int precision, int nx, int ny, int
     if (cudaSetDevice(device) != cudaSuccess) return OOTS_E_CUDA;
     DevSetup &S = g_setup[device];
     int rc = OOTS_OK;
+    std::unique_lock<std::mutex> setup_lock(g_setup_mutex);
     if (!S.ready) {
         // once per device, with the device current: the device address of the
         // static scratch (its host-side name is only a stand-in), the kernels'
@@ -226,6 +238,7 @@ extern "C" int oots_trace_noalloc(int device, int precision, int nx, int ny, int
             S.ready = true;
         }
     }
+    setup_lock.unlock();
     cudaStream_t st = (cudaStream_t)stream;
     if (rc == OOTS_OK) {
         int r = precision == OOTS_FP64
@@ -237,7 +250,7 @@ extern "C" int oots_trace_noalloc(int device, int precision, int nx, int ny, int
             snprintf(msg, sizeof(msg),
                      "oots_trace_noalloc: the grid needs %d tiles of 16x8x8 cells; the %zu MiB static scratch holds "
                      "at most %lld (%s)", -1000 - r, kScratchBytes >> 20,
-                     (long long)((kScratchBytes - 65536) / (precision == OOTS_FP64 ? tile_bytes<double>() : tile_bytes<float>())),
+                     precision == OOTS_FP64 ? max_tiles<double>() : max_tiles<float>(),
                      precision == OOTS_FP64 ? "FP64" : "mixed");
             oots_set_error_text(msg);
             rc = OOTS_E_INVAL;

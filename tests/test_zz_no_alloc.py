@@ -1,5 +1,6 @@
 """The allocation-free trace entry point (oots_trace_noalloc), for callers
-that cannot allocate device memory (graph captures, fixed memory arenas):
+that cannot allocate device memory (code inside a fixed memory arena, or a
+host whose allocator must not be re-entered):
 through the C ABI it must give the same entry columns as the context API's
 trace, on two calls in a row sharing its static scratch.
 
