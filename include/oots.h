@@ -245,6 +245,12 @@ int oots_batch_create(oots_batch **out, oots_ctx *const *ctxs, int n);
  * substeps each context took. */
 int oots_batch_advance(oots_batch *b, const double *t_end_each, long long *nsub_out);
 
+/* Enqueue exactly n substeps of every context of the batch toward its own
+ * end time t_end_each[i] (graph replays on the first context's stream; a grid
+ * that reaches its end time does no further work) and return without
+ * waiting.  Pair with oots_synchronize on the first context. */
+int oots_batch_run_substeps(oots_batch *b, long long n, const double *t_end_each);
+
 int oots_batch_destroy(oots_batch *b);
 
 /* ---- tuning and diagnostics ----------------------------------------------------------------- */

@@ -11,6 +11,8 @@
 // of every panel are evaluated one per lane, so the few slow cells near the
 // ionisation front neither hold up warps of fast cells nor run their node
 // evaluations one after another.
+#include <algorithm>
+
 #include "common.cuh"
 #include "integrator.cuh"
 #include "kernels.h"
@@ -346,6 +348,461 @@ cell_general_kernel(const GridDev<Real> *grids, int ngrid, const long long *offs
     }
 }
 
+// ---------------------------------------------------------------------------
+// Many sources per grid: per-cell source selection
+// ---------------------------------------------------------------------------
+// A source can raise a cell's photoionisation rate per unit neutral fraction
+// by at most amp = A b (monochromatic) or A p sigma0 b (tabulated: no
+// cross-section exceeds sigma0).  Both equal qfac sigma0 dx p / r2 (r2 = 1 for
+// a plane source), p the fraction of the source's photons that reach the
+// cell.  A source with amp h at most a thousandth of the rounding cannot move
+// x over a step h, so it is left out of the cell's rate (the rule by which the
+// single-source closed forms call a cell photon-free).  The bound is formed in
+// float, from the table node at or below the column (P falls as N grows); the
+// rates of the sources kept are then formed exactly, in a few registers.
+constexpr int NACT = 4;        // sources the closed-form passes hold in registers
+constexpr int NACT_GEN = 8;    // sources the general pass holds in registers
+
+// ln P(N)/Q rounded up: the node value one interval below N's
+template <typename Real>
+__device__ __forceinline__ float lnp_upper(const DevTable<Real> &T, Real N)
+{
+    if (!(N > T.N0)) return 0.0f;
+    if (N > T.Nhi) return -__int_as_float(0x7f800000);
+    int k = (int)floorf((__logf((float)N) - (float)T.lnN_lo) * (float)T.inv_dl) - 1;
+    k = k < 0 ? 0 : (k > T.K - 1 ? T.K - 1 : k);
+    return (float)T.L[k];
+}
+
+// Octant-local indices of cell (X,Y,Z) for source s and r2 = |c|^2 in units
+// of dx^2 (1 for a plane source, whose rate shares photons per unit area).
+template <typename Real>
+__device__ __forceinline__ float src_cell(const GridDev<Real> &G, int s, int X, int Y, int Z, int &i, int &j, int &k)
+{
+    i = X >= G.vtx[s][0] ? X - G.vtx[s][0] : G.vtx[s][0] - 1 - X;
+    j = Y >= G.vtx[s][1] ? Y - G.vtx[s][1] : G.vtx[s][1] - 1 - Y;
+    k = Z >= G.vtx[s][2] ? Z - G.vtx[s][2] : G.vtx[s][2] - 1 - Z;
+    if (G.pcode[s]) return 1.0f;
+    const float c0 = i + 0.5f, c1 = j + 0.5f, c2 = k + 0.5f;
+    return c0 * c0 + c1 * c1 + c2 * c2;
+}
+
+// ln of the bound amp of source s (entry column N) at a cell with r2
+template <typename Real>
+__device__ __forceinline__ float src_lnamp(const GridDev<Real> &G, const DevTable<Real> *tabs, int s, float r2, Real N)
+{
+    const float lnp = G.tab[s] < 0 ? -(float)G.sigma0 * (float)N : lnp_upper(tabs[G.tab[s]], N);
+    return G.lnamp0[s] + lnp - __logf(r2);
+}
+
+// Rate parameters of the sources whose bound exceeds e^lnthr, into
+// r[0 .. NK-1] (indices fixed at compile time, so r stays in registers).
+// Returns how many there are; NK + 1 when there are more than NK.
+template <typename Real, int NK>
+__device__ __forceinline__ int gather_rates(const GridDev<Real> &G, const Real *Ncol, const DevTable<Real> *tabs,
+                                            int X, int Y, int Z, long long g, Real n, float lnthr, SrcRate<Real> *r)
+{
+    int cnt = 0;
+    for (int s = 0; s < G.nsrc; s++) {
+        int i, j, k;
+        const float r2 = src_cell(G, s, X, Y, Z, i, j, k);
+        const Real N = Ncol[(long long)s * G.ncell + g];
+        if (!(src_lnamp(G, tabs, s, r2, N) > lnthr)) continue;
+        if (cnt == NK) return NK + 1;
+        SrcRate<Real> t;
+        src_rate<Real>(t, G.qfac[s], G.tab[s], G.sigma0, G.dx, n, G.pcode[s] != 0, i, j, k, N, tabs);
+#pragma unroll
+        for (int q = 0; q < NK; q++)
+            if (q == cnt) r[q] = t;
+        cnt++;
+    }
+    return cnt;
+}
+
+// ln(1e-3 eps / h): the selection threshold for a step h (-inf: keep every source)
+template <typename Real> __device__ __forceinline__ float lnthr_step(double h)
+{
+    if (!(h > 0.0) || !(h < 1e290)) return -__int_as_float(0x7f800000);
+    return (float)(log(1e-3 * (double)RealLimits<Real>::eps()) - log(h));
+}
+
+// Closed forms from F(x0), F'(x0) alone (no per-source rates): photon-free,
+// at the root within rounding, or slow enough for the linearised step.  bm
+// bounds the optical-depth scale of every source per unit x.  Returns true
+// when the cell is done.
+template <typename Real>
+__device__ __forceinline__ bool closed_form_from_F(Real c, Real x0, Real h, Real F0, Real dF0, Real bm,
+                                                   IntResult<Real> &R)
+{
+    const Real f0 = -F0 + c * (Real(1) - x0) * (Real(1) - x0);
+    if (m_abs(f0) <= Real(32) * RealLimits<Real>::eps() * (m_abs(F0) + c * (Real(1) - x0) * (Real(1) - x0))) {
+        R.x = x0;
+        R.IR = h * c * (Real(1) - x0) * (Real(1) - x0);
+        return true;
+    }
+    const Real df0 = -dF0 - Real(2) * c * (Real(1) - x0);
+    const Real z = h * df0;
+    if (!(m_abs(z) <= IntCfg<Real>::zlin())) return false;
+    const Real phi = (m_abs(z) > Real(1e-8)) ? m_expm1(z) / z : Real(1) + Real(0.5) * z;
+    const Real dx = h * f0 * phi;
+    const Real adx = m_abs(dx);
+    if (bm * adx <= IntCfg<Real>::zlin() && c * h * adx <= IntCfg<Real>::zlin() * IntCfg<Real>::zlin() &&
+        x0 + dx >= Real(0) && x0 + dx <= Real(1)) {
+        R.x = x0 + dx;
+        const Real xm = x0 + Real(0.5) * dx;
+        R.IR = h * c * (Real(1) - xm) * (Real(1) - xm);
+        return true;
+    }
+    return false;
+}
+
+// Per-cell passes of grids with several sources.
+//
+// RATEDT (Eq. 4 minimum over cells) first bounds every source's rate at the
+// cell, then forms the exact |dx/dt| only where the cell can set the step: a
+// cell whose upper bound of |dx/dt| gives a criterion above the hint H
+// (four times the previous substep's step) cannot be the minimum if the
+// minimum is below H, and sources whose bound times H is below a thousandth
+// of the rounding are left out of the sum (they change the limiting |dx/dt|
+// by far less than its rounding).  A second, verifying launch (verify = 1)
+// recomputes every cell without hint when the minimum came out above H; it
+// returns at once otherwise.  RATEDT caches F, F' (NaN where it skipped the
+// cell) and the sum of the sources' bounds for the step that follows on the
+// same columns (A3's half step, A2's full step).  That step settles
+// photon-free and slow cells from the cache alone; A3's full step (new
+// columns) and the cells the cache does not settle select their sources for
+// the step and run the closed forms on them.  The rest go to the general pass.
+// The kernel walks 256-cell chunks with a stride of the grid size.
+template <typename Real, int OP>
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_kernel(const GridDev<Real> *grids, int ngrid,
+                                                         const long long *offsets, long long total,
+                                                         const DevTable<Real> *tabs, unsigned *queue,
+                                                         unsigned *qcount, Real *rcache, int use_cache, int verify)
+{
+    __shared__ double sh[32];
+    __shared__ int s_grid_lo, s_grid_hi, s_skip;
+    __shared__ double s_h, s_hint;
+    __shared__ float s_lnthr, s_f[4];
+    constexpr bool F32 = sizeof(Real) == 4;
+    const long long nchunk = (total + 255) / 256;
+    if (OP == OP_RATEDT && verify) {
+        // nothing to do unless some grid's first-pass minimum exceeded its hint
+        if (threadIdx.x == 0) {
+            int any = 0;
+            for (int q = 0; q < ngrid && !any; q++) {
+                const DevState *sq = grids[q].st;
+                const double d = sq->dt;
+                const unsigned long long b = sq->dt_bits;
+                if (sq->done || !(d > 0.0)) continue;            // no hint was used
+                any = b == 0xffffffffffffffffull || __longlong_as_double((long long)b) > 4.0 * d;
+            }
+            s_skip = any;
+        }
+        __syncthreads();
+        if (!s_skip) return;
+    }
+    for (long long chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
+    const long long base = chunk * 256;
+    if (threadIdx.x == 0) {
+        long long last = base + blockDim.x - 1;
+        if (last >= total) last = total - 1;
+        s_grid_lo = find_grid(offsets, ngrid, base);
+        s_grid_hi = find_grid(offsets, ngrid, last);
+    }
+    __syncthreads();
+    for (int gi = s_grid_lo; gi <= s_grid_hi; gi++) {
+        const GridDev<Real> &G = grids[gi];
+        DevState *st = G.st;
+        if (threadIdx.x == 0) {
+            const double d = st->dt;
+            const double h = OP == OP_HALF ? 0.5 * d : d;
+            s_h = h;
+            s_skip = 0;
+            if (OP == OP_RATEDT) {
+                // st->dt still holds the previous substep's step here
+                double hint = d > 0.0 ? 4.0 * d : __longlong_as_double(0x7ff0000000000000ll);
+                if (verify) {
+                    // a minimum at or below the hint stands: every cell the first pass
+                    // skipped asks for more.  (Other blocks of this pass may have lowered
+                    // it meanwhile; that only means the same.)
+                    const unsigned long long b = st->dt_bits;
+                    const double mn = b == 0xffffffffffffffffull ? __longlong_as_double(0x7ff0000000000000ll)
+                                                                : __longlong_as_double((long long)b);
+                    if (!(d > 0.0) || mn <= hint) s_skip = 1;
+                    hint = __longlong_as_double(0x7ff0000000000000ll);
+                }
+                s_hint = hint;
+                s_lnthr = lnthr_step<Real>(hint);
+            } else {
+                s_lnthr = lnthr_step<Real>(h);
+            }
+            s_f[0] = float(h);
+            s_f[1] = float(st->K1);
+            s_f[2] = float(st->K3);
+            s_f[3] = float(st->K4);
+        }
+        __syncthreads();
+        if (s_skip) { __syncthreads(); continue; }
+        const long long idx = base + threadIdx.x;
+        const bool mine = idx < total && idx >= offsets[gi] && (gi + 1 >= ngrid || idx < offsets[gi + 1]);
+        const bool stepping = s_h > 0.0;
+        const bool active = mine && (OP == OP_RATEDT ? !st->done : stepping);
+        double dtmin = __longlong_as_double(0x7ff0000000000000ll);
+        float dtmin_f = __int_as_float(0x7f800000);
+        float ions_f = 0.0f, rec_f = 0.0f;
+        double ions = 0.0, rec = 0.0;
+        bool defer = false;
+        if (active) {
+            const long long g = idx - offsets[gi];
+            const int X = (int)(g % G.nx);
+            const int Y = (int)((g / G.nx) % G.ny);
+            const int Z = (int)(g / ((long long)G.nx * G.ny));
+            const Real n = G.n ? G.n[g] : G.n_uniform;
+            const Real x0 = G.x[g];
+            const Real c = G.alpha * n;
+            const float lnthr = s_lnthr;
+            if (OP == OP_RATEDT) {
+                // Eq. 4 with T fixed: K1 t_rec, K3 max(0.05, x)/|dx/dt|, K4/|dx/dt|
+                float ampsum = 0.0f;
+                for (int s = 0; s < G.nsrc; s++) {
+                    int i, j, k;
+                    const float r2 = src_cell(G, s, X, Y, Z, i, j, k);
+                    ampsum += __expf(src_lnamp(G, tabs, s, r2, G.N1[(long long)s * G.ncell + g]));
+                }
+                // |dx/dt| <= F + c (1-x)^2 with F <= x0 sum(amp): the smallest step the cell could ask for
+                const double xdu = double(ampsum) * double(x0) * 1.0001 + double(c) * double(Real(1) - x0) * double(Real(1) - x0);
+                double lowest = __longlong_as_double(0x7ff0000000000000ll);
+                if (xdu > 0.0) {
+                    if (st->K3 > 0) lowest = fmin(lowest, st->K3 * fmax(0.05, double(x0)) / xdu);
+                    if (st->K4 > 0) lowest = fmin(lowest, st->K4 / xdu);
+                }
+                const bool exact = lowest < s_hint;
+                Real F = Real(0), dF = Real(0);
+                if (exact) {
+                    for (int s = 0; s < G.nsrc; s++) {
+                        int i, j, k;
+                        const float r2 = src_cell(G, s, X, Y, Z, i, j, k);
+                        const Real N = G.N1[(long long)s * G.ncell + g];
+                        if (!(src_lnamp(G, tabs, s, r2, N) > lnthr)) continue;
+                        SrcRate<Real> t;
+                        src_rate<Real>(t, G.qfac[s], G.tab[s], G.sigma0, G.dx, n, G.pcode[s] != 0, i, j, k, N, tabs);
+                        CellODE<Real> C1;
+                        C1.ns = 1; C1.c = c; C1.b0 = Real(0); C1.r = &t; C1.tabs = tabs;
+                        Real Fs, dFs;
+                        ode_F<Real, 1>(C1, x0, &Fs, &dFs);
+                        F += Fs;
+                        dF += dFs;
+                    }
+                }
+                if (rcache) {
+                    rcache[idx] = exact ? F : __int_as_float(0x7fc00000);
+                    rcache[total + idx] = dF;
+                    rcache[2 * total + idx] = Real(ampsum);
+                }
+                if (F32) {
+                    if (s_f[1] > 0.0f) dtmin_f = fminf(dtmin_f, s_f[1] / (float(G.alpha) * float(n)));
+                    const float xd = fabsf(float(-F + c * (Real(1) - x0) * (Real(1) - x0)));
+                    if (exact && xd > 0.0f) {
+                        if (s_f[2] > 0.0f) dtmin_f = fminf(dtmin_f, s_f[2] * fmaxf(0.05f, float(x0)) / xd);
+                        if (s_f[3] > 0.0f) dtmin_f = fminf(dtmin_f, s_f[3] / xd);
+                    }
+                } else {
+                    if (st->K1 > 0) dtmin = fmin(dtmin, st->K1 / (double(G.alpha) * double(n)));
+                    const double xd = fabs((double)(-F + c * (Real(1) - x0) * (Real(1) - x0)));
+                    if (exact && xd > 0) {
+                        if (st->K3 > 0) dtmin = fmin(dtmin, st->K3 * fmax(0.05, (double)x0) / xd);
+                        if (st->K4 > 0) dtmin = fmin(dtmin, st->K4 / xd);
+                    }
+                }
+            } else {
+                const Real h = F32 ? Real(s_f[0]) : Real(s_h);
+                IntResult<Real> R;
+                R.x = x0; R.IR = Real(0); R.lnfav = Real(0);
+                bool done = false;
+                Real F0 = Real(0), dF0 = Real(0);
+                bool have_F = false;
+                const bool cached = (OP == OP_HALF || OP == OP_FULL1) && use_cache && rcache;
+                if (cached) {
+                    const Real ampsum = rcache[2 * total + idx];
+                    if (!(ampsum * h > Real(1e-3) * RealLimits<Real>::eps())) {
+                        // photon-free: du/dt = -c u^2, u = 1 - x
+                        const Real u0 = Real(1) - x0;
+                        const Real u = u0 / (Real(1) + c * u0 * h);
+                        R.x = Real(1) - u;
+                        R.IR = u0 - u;
+                        done = true;
+                    } else {
+                        F0 = rcache[idx];
+                        dF0 = rcache[total + idx];
+                        if (F0 == F0) {        // the dt pass formed F (not skipped)
+                            have_F = true;
+                            // no source's optical depth per unit x exceeds sigma0 n dx sqrt(3)
+                            const Real bm = G.sigma0 * n * G.dx * Real(1.7320508075688772);
+                            done = closed_form_from_F<Real>(c, x0, h, F0, dF0, bm, R);
+                        }
+                    }
+                }
+                if (!done) {
+                    SrcRate<Real> r[NACT];
+                    const Real *Ncol = (OP == OP_FULL2) ? G.N2 : G.N1;
+                    const int na = gather_rates<Real, NACT>(G, Ncol, tabs, X, Y, Z, g, n, lnthr, r);
+                    if (na <= NACT) {
+                        CellODE<Real> C;
+                        C.ns = na; C.c = c; C.b0 = Real(0); C.r = r; C.tabs = tabs;
+                        Real f0;
+                        done = integrate_prelude<Real, NACT>(C, x0, h, G.sigma0, R, F0, dF0, f0, have_F && na > 0);
+                    }
+                }
+                if (done) {
+                    if (OP == OP_HALF) {
+                        const_cast<Real *>(G.xh)[g] = R.x;
+                    } else {
+                        G.xout[g] = R.x;
+                        if (F32) {
+                            ions_f = float(n) * (float(x0) - float(R.x));
+                            rec_f = float(n) * float(R.IR);
+                        } else {
+                            const double nV = double(n) * st->cell_volume;
+                            ions = nV * (double(x0) - double(R.x));
+                            rec = nV * double(R.IR);
+                        }
+                    }
+                } else {
+                    defer = true;
+                }
+            }
+        }
+        if (OP != OP_RATEDT) {
+            const unsigned m = __ballot_sync(0xffffffffu, defer);
+            if (m) {
+                const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+                unsigned qb = 0;
+                if (lane == leader) qb = atomicAdd(qcount + (OP == OP_HALF ? 0 : 1), (unsigned)__popc(m));
+                qb = __shfl_sync(0xffffffffu, qb, leader);
+                if (defer) queue[qb + __popc(m & ((1u << lane) - 1u))] = (unsigned)idx;
+            }
+        }
+        if (OP == OP_RATEDT) {
+            if (F32) {
+                for (int o = 16; o > 0; o >>= 1) dtmin_f = fminf(dtmin_f, __shfl_down_sync(0xffffffffu, dtmin_f, o));
+                if ((threadIdx.x & 31) == 0) dtmin = double(dtmin_f);
+            } else {
+                for (int o = 16; o > 0; o >>= 1) dtmin = fmin(dtmin, __shfl_down_sync(0xffffffffu, dtmin, o));
+            }
+            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+            __syncthreads();
+            if (lane == 0) sh[wid] = dtmin;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double mn = sh[0];
+                for (int w = 1; w < (int)(blockDim.x >> 5); w++) mn = fmin(mn, sh[w]);
+                if (mn < 1e300) atomicMin(&st->dt_bits, (unsigned long long)__double_as_longlong(mn));
+            }
+        } else if (OP == OP_FULL1 || OP == OP_FULL2) {
+            double si = ions, sr = rec;
+            if (F32) block_sum2_f(ions_f, rec_f, st->cell_volume, si, sr, sh);
+            else block_sum2(si, sr, sh);
+            if (threadIdx.x == 0 && (si != 0.0 || sr != 0.0)) {
+                atomicAdd(&st->bud_step[1], si + sr);
+                atomicAdd(&st->bud_step[2], si);
+                atomicAdd(&st->bud_step[3], sr);
+            }
+        }
+        __syncthreads();
+    }
+    __syncthreads();
+    }
+}
+
+// General pass of grids with several sources: one lane group per queued
+// cell, as cell_general_kernel, with the sources selected for the step in
+// registers (all of them, in local memory, for the rare cell that more than
+// NACT_GEN sources light).
+template <typename Real, int OP>
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2)
+cell_multi_general_kernel(const GridDev<Real> *grids, int ngrid, const long long *offsets, const DevTable<Real> *tabs,
+                          const unsigned *queue, unsigned *qcount)
+{
+    __shared__ double s_ions[8], s_rec[8];
+    __shared__ int s_gid[8];
+    constexpr int W = GroupWidth<Real>::value;
+    const int lane32 = threadIdx.x & 31;
+    const int gbase = lane32 & ~(W - 1), lane = lane32 - gbase;
+    const unsigned gmask = W == 32 ? 0xffffffffu : (0xffffu << gbase);
+    if (OP != OP_HALF) {
+        if (threadIdx.x < 8) { s_ions[threadIdx.x] = 0.0; s_rec[threadIdx.x] = 0.0; s_gid[threadIdx.x] = -1; }
+        __syncthreads();
+    }
+    const int qi = OP == OP_HALF ? 0 : 1;
+    const unsigned nq = qcount[qi];
+    for (;;) {
+        unsigned q = 0;
+        if (lane == 0) q = atomicAdd(&qcount[2 + qi], 1u);
+        q = __shfl_sync(gmask, q, gbase);
+        if (q >= nq) break;
+        const long long idx = queue[q];
+        const int gi = find_grid(offsets, ngrid, idx);
+        const GridDev<Real> &G = grids[gi];
+        DevState *st = G.st;
+        const double dtd = st->dt;
+        const long long g = idx - offsets[gi];
+        const int X = (int)(g % G.nx);
+        const int Y = (int)((g / G.nx) % G.ny);
+        const int Z = (int)(g / ((long long)G.nx * G.ny));
+        const Real n = G.n ? G.n[g] : G.n_uniform;
+        const Real x0 = G.x[g];
+        const Real *Ncol = (OP == OP_FULL2) ? G.N2 : G.N1;
+        const double hd = OP == OP_HALF ? 0.5 * dtd : dtd;
+        const Real h = Real(hd);
+        const float lnthr = lnthr_step<Real>(hd);
+        IntResult<Real> R;
+        Real F0, dF0, f0;
+        SrcRate<Real> r[NACT_GEN];
+        const int na = gather_rates<Real, NACT_GEN>(G, Ncol, tabs, X, Y, Z, g, n, lnthr, r);
+        if (na <= NACT_GEN) {
+            CellODE<Real> C;
+            C.ns = na; C.c = G.alpha * n; C.b0 = Real(0); C.r = r; C.tabs = tabs;
+            if (!integrate_prelude<Real, NACT_GEN>(C, x0, h, G.sigma0, R, F0, dF0, f0))
+                R = integrate_general<Real, NACT_GEN>(C, x0, h, G.sigma0, R, F0, dF0, f0, GroupEval<W>{lane, gbase, gmask});
+        } else {
+            SrcRate<Real> ra[MAX_SRC];
+            CellODE<Real> C;
+            C.ns = cell_rates<Real, MAX_SRC>(G, Ncol, tabs, X, Y, Z, g, n, ra);
+            C.c = G.alpha * n; C.b0 = Real(0); C.r = ra; C.tabs = tabs;
+            if (!integrate_prelude<Real, MAX_SRC>(C, x0, h, G.sigma0, R, F0, dF0, f0))
+                R = integrate_general<Real, MAX_SRC>(C, x0, h, G.sigma0, R, F0, dF0, f0, GroupEval<W>{lane, gbase, gmask});
+        }
+        if (lane == 0) {
+            if (OP == OP_HALF) {
+                const_cast<Real *>(G.xh)[g] = R.x;
+            } else {
+                G.xout[g] = R.x;
+                const double nV = double(n) * st->cell_volume;
+                const double ions = nV * (double(x0) - double(R.x)), rec = nV * double(R.IR);
+                const int slot = gi & 7;
+                const int owner = atomicCAS(&s_gid[slot], -1, gi);
+                if (owner == -1 || owner == gi) {
+                    atomicAdd(&s_ions[slot], ions);
+                    atomicAdd(&s_rec[slot], rec);
+                } else {
+                    atomicAdd(&st->bud_step[1], ions + rec);
+                    atomicAdd(&st->bud_step[2], ions);
+                    atomicAdd(&st->bud_step[3], rec);
+                }
+            }
+        }
+    }
+    if (OP != OP_HALF) {
+        __syncthreads();
+        if (threadIdx.x < 8 && s_gid[threadIdx.x] >= 0) {
+            DevState *st = grids[s_gid[threadIdx.x]].st;
+            atomicAdd(&st->bud_step[1], s_ions[threadIdx.x] + s_rec[threadIdx.x]);
+            atomicAdd(&st->bud_step[2], s_ions[threadIdx.x]);
+            atomicAdd(&st->bud_step[3], s_rec[threadIdx.x]);
+        }
+    }
+}
+
 // stage 0: choose dt (Eq. 4 minimum or fixed, capped at t_end - t) and reset the step budget
 // stage 1: close the substep (t += dt, totals, done flag)
 template <typename Real>
@@ -410,8 +867,24 @@ cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *
     if (nsmax <= 1)
         return launch_cell_ns<Real, 1>(grids, ngrid, offsets, total, tabs, op, queue, qcount, qrec, rcache,
                                        use_cache && rcache, gen_blocks, s);
-    return launch_cell_ns<Real, MAX_SRC>(grids, ngrid, offsets, total, tabs, op, queue, qcount, nullptr, nullptr, 0,
-                                         gen_blocks, s);
+    const int bs = 256;
+    const long long nb = (total + bs - 1) / bs;
+    const int uc = use_cache && rcache ? 1 : 0;
+    switch (op) {
+    case OP_RATEDT:
+        cell_multi_kernel<Real, OP_RATEDT><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0);
+        // the verifying pass: a few resident blocks that return unless the minimum exceeded the hint
+        cell_multi_kernel<Real, OP_RATEDT><<<(unsigned)std::min<long long>(nb, 8LL * gen_blocks), bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 1);
+        break;
+    case OP_HALF: cell_multi_kernel<Real, OP_HALF><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0); break;
+    case OP_FULL1: cell_multi_kernel<Real, OP_FULL1><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0); break;
+    case OP_FULL2: cell_multi_kernel<Real, OP_FULL2><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0); break;
+    case OP_HALF | OP_GENERAL: cell_multi_general_kernel<Real, OP_HALF><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
+    case OP_FULL1 | OP_GENERAL: cell_multi_general_kernel<Real, OP_FULL1><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
+    case OP_FULL2 | OP_GENERAL: cell_multi_general_kernel<Real, OP_FULL2><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 template <typename Real> size_t queue_record_bytes() { return QREC * sizeof(Real); }
@@ -423,7 +896,7 @@ int cell_general_occupancy(int nsmax)
     int nb = 0;
     cudaError_t e = nsmax <= 1
         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_general_kernel<Real, OP_FULL2, 1>, 256, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_general_kernel<Real, OP_FULL2, MAX_SRC>, 256, 0);
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, cell_multi_general_kernel<Real, OP_FULL2>, 256, 0);
     return (e == cudaSuccess && nb > 0) ? nb : 1;
 }
 

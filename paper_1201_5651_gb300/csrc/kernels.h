@@ -20,8 +20,11 @@ template <typename Real> struct ColT;
     X(4, 8, 8, 8)      \
     X(5, 16, 16, 8)    \
     X(6, 8, 8, 4)
-enum { NUM_SHAPES = 7 };
-static const int SHAPE_DIMS[NUM_SHAPES][3] = {{16, 8, 8}, {16, 8, 4}, {16, 16, 16}, {32, 8, 4}, {8, 8, 8}, {16, 16, 8}, {8, 8, 4}};
+// Shape 7 tiles the octants like shape 4 (8 x 8 x 8) but traces them with the
+// throughput kernel (whole tiles, 64 threads, layer sweeps off the diagonal
+// planes; sweep_tp.cuh); the implicit sweep (A1) runs shape 4's kernel on it.
+enum { NUM_SHAPES = 8, SHAPE_TP8 = 7 };
+static const int SHAPE_DIMS[NUM_SHAPES][3] = {{16, 8, 8}, {16, 8, 4}, {16, 16, 16}, {32, 8, 4}, {8, 8, 8}, {16, 16, 8}, {8, 8, 4}, {8, 8, 8}};
 
 template <typename Real> struct SweepParams {
     const GridDev<Real> *grids;
@@ -64,10 +67,11 @@ cudaError_t launch_plane(const GridDev<Real> *grids, const PlaneJob *jobs, int n
 enum { OP_RATEDT = 0, OP_HALF = 1, OP_FULL1 = 2, OP_FULL2 = 3, OP_GENERAL = 16 };
 // qrec: per queue slot the closed-form pass's rates and f(x0) of single-source
 // cells (queue_record_bytes each), so the general pass starts at the root
-// search.  rcache: 3 x total values per cell (transmitted fraction, F(x0),
-// F'(x0)) that the dt pass writes and the half step (A3) or full step (A2)
-// of the same substep reads when use_cache is set.  Both unused (may be null)
-// when nsmax > 1.
+// search (unused, may be null, when nsmax > 1).  rcache: 3 x total values per
+// cell that the dt pass writes and the half step (A3) or full step (A2) of
+// the same substep reads when use_cache is set: the transmitted fraction,
+// F(x0) and F'(x0) of single-source grids; F(x0), F'(x0) and the sum of the
+// sources' rate bounds when nsmax > 1 (the full step then recomputes).
 template <typename Real>
 cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
                         const DevTable<Real> *tabs, int op, int nsmax, unsigned *queue, unsigned *qcount,

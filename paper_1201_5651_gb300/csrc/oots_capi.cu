@@ -109,6 +109,8 @@ struct oots_ctx {
     int sweep_chunk = 0;               // planes per progress step of the sweep (0: default)
     size_t rsize = 8;
     void *d_x = nullptr, *d_n = nullptr, *d_xh = nullptr, *d_N1 = nullptr, *d_N2 = nullptr;
+    void *d_stage = nullptr;           // ncell doubles: host arrays pass through it (allocated on first use)
+    long long *d_bad = nullptr;        // first cell a device-side check rejected
     int nsrc_alloc = 0;
     DevState *d_st = nullptr;
     int *d_err = nullptr;
@@ -256,7 +258,9 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
             for (int s = 0; s < G.nsrc; s++) {
                 const SourceH &S = c->src[s];
                 for (int a = 0; a < 3; a++) G.vtx[s][a] = S.pcode ? 0 : S.v[a];
-                G.qfac[s] = S.pcode ? Real(S.Q / c->dx) : Real(S.Q / (4.0 * M_PI * c->dx * c->dx * c->dx));
+                const double qf = S.pcode ? S.Q / c->dx : S.Q / (4.0 * M_PI * c->dx * c->dx * c->dx);
+                G.qfac[s] = Real(qf);
+                G.lnamp0[s] = (float)std::log(qf * c->sigma0 * c->dx);
                 G.pcode[s] = (unsigned char)S.pcode;
                 if (S.spectrum == OOTS_MONO) G.tab[s] = -1;
                 else {
@@ -329,7 +333,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         if (total > 0xffffffffll) return fail(OOTS_E_INVAL, "%lld cells in one call (the queue holds 32-bit indices)", total);
         CU(cudaMalloc(&d_queue, (size_t)std::max(total, 1ll) * sizeof(unsigned)));
         if (nsmax <= 1) CU(cudaMalloc(&d_qrec, (size_t)std::max(total, 1ll) * queue_record_bytes<Real>()));
-        if (nsmax <= 1) CU(cudaMalloc(&d_rcache, (size_t)std::max(total, 1ll) * 3 * sizeof(Real)));
+        CU(cudaMalloc(&d_rcache, (size_t)std::max(total, 1ll) * 3 * sizeof(Real)));
         CU(cudaMalloc(&d_qcount, 8 * sizeof(unsigned)));
         CU(cudaMemset(d_qcount, 0, 8 * sizeof(unsigned)));
         if (!jobs.empty()) {
@@ -588,34 +592,95 @@ static int prepare(oots_ctx *c)
     return OOTS_OK;
 }
 
-static int to_real_upload(oots_ctx *c, void *dst, const double *src, double uniform)
+// Host arrays move through a device staging buffer of doubles: one copy at the
+// link's bandwidth, then the checks and the conversion to the state's
+// precision run on the device (at 512^3 a host loop over the cells would
+// take longer than several substeps).
+__global__ void fill_kernel(void *dst, int dd, double v, long long n)
 {
-    std::vector<double> tmp;
-    const double *p = src;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (dd == 0) ((double *)dst)[i] = v;
+    else ((float *)dst)[i] = (float)v;
+}
+
+// kind 0: neutral fraction, values in [0, 1]; kind 1: density, finite and > 0.
+// Records the smallest failing index.
+__global__ void check_kernel(const double *v, long long n, int kind, long long *bad)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double a = v[i];
+    const bool ok = kind == 0 ? (a >= 0.0 && a <= 1.0) : (a > 0.0 && a <= 1.7976931348623157e308);
+    if (!ok) atomicMin((unsigned long long *)bad, (unsigned long long)i);
+}
+
+__global__ void convert_kernel(const void *src, int sd, void *dst, int dd, long long n)
+{
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = sd == 0 ? ((const double *)src)[i] : (double)((const float *)src)[i];
+    if (dd == 0) ((double *)dst)[i] = v;
+    else ((float *)dst)[i] = (float)v;
+}
+
+static unsigned blocks_for(long long n) { return (unsigned)((n + 255) / 256); }
+
+static int ensure_stage(oots_ctx *c)
+{
+    if (c->d_stage) return OOTS_OK;
+    if (cudaMalloc(&c->d_stage, (size_t)c->ncell * sizeof(double)) != cudaSuccess) {
+        c->d_stage = nullptr;
+        cudaGetLastError();
+        return fail(OOTS_E_NOMEM, "staging buffer of %lld cells", c->ncell);
+    }
+    return OOTS_OK;
+}
+
+// Upload a host array (checked on the device first: kind as check_kernel) or
+// a uniform value into dst, in the state's precision.  *bad_out receives the
+// first rejected cell (-1: none); dst is untouched when a cell is rejected.
+static int to_real_upload(oots_ctx *c, void *dst, const double *src, double uniform, int kind, long long *bad_out)
+{
+    const int own = c->precision == OOTS_FP64 ? 0 : 1;
+    *bad_out = -1;
     if (!src) {
-        tmp.assign((size_t)c->ncell, uniform);
-        p = tmp.data();
+        fill_kernel<<<blocks_for(c->ncell), 256, 0, c->stream>>>(dst, own, uniform, c->ncell);
+        CU(cudaGetLastError());
+        CU(cudaStreamSynchronize(c->stream));
+        return OOTS_OK;
     }
-    if (c->precision == OOTS_FP64) {
-        CU(cudaMemcpy(dst, p, (size_t)c->ncell * sizeof(double), cudaMemcpyHostToDevice));
-    } else {
-        std::vector<float> f((size_t)c->ncell);
-        for (long long i = 0; i < c->ncell; i++) f[i] = (float)p[i];
-        CU(cudaMemcpy(dst, f.data(), (size_t)c->ncell * sizeof(float), cudaMemcpyHostToDevice));
+    int rc = ensure_stage(c);
+    if (rc) return rc;
+    CU(cudaMemcpyAsync(c->d_stage, src, (size_t)c->ncell * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemsetAsync(c->d_bad, 0xff, sizeof(long long), c->stream));
+    check_kernel<<<blocks_for(c->ncell), 256, 0, c->stream>>>((const double *)c->d_stage, c->ncell, kind, c->d_bad);
+    CU(cudaGetLastError());
+    unsigned long long bad = 0;
+    CU(cudaMemcpyAsync(&bad, c->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (bad != 0xffffffffffffffffull) {
+        *bad_out = (long long)bad;
+        return OOTS_OK;
     }
+    convert_kernel<<<blocks_for(c->ncell), 256, 0, c->stream>>>(c->d_stage, 0, dst, own, c->ncell);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(c->stream));
     return OOTS_OK;
 }
 
 static int download_real(oots_ctx *c, const void *srcp, double *out)
 {
-    CU(cudaStreamSynchronize(c->stream));
     if (c->precision == OOTS_FP64) {
-        CU(cudaMemcpy(out, srcp, (size_t)c->ncell * sizeof(double), cudaMemcpyDeviceToHost));
+        CU(cudaMemcpyAsync(out, srcp, (size_t)c->ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     } else {
-        std::vector<float> f((size_t)c->ncell);
-        CU(cudaMemcpy(f.data(), srcp, (size_t)c->ncell * sizeof(float), cudaMemcpyDeviceToHost));
-        for (long long i = 0; i < c->ncell; i++) out[i] = (double)f[i];
+        int rc = ensure_stage(c);
+        if (rc) return rc;
+        convert_kernel<<<blocks_for(c->ncell), 256, 0, c->stream>>>(srcp, 1, c->d_stage, 0, c->ncell);
+        CU(cudaGetLastError());
+        CU(cudaMemcpyAsync(out, c->d_stage, (size_t)c->ncell * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     }
+    CU(cudaStreamSynchronize(c->stream));
     return OOTS_OK;
 }
 
@@ -648,7 +713,8 @@ int oots_create(oots_ctx **out, int device, int precision)
         return fail(OOTS_E_CUDA, "stream creation failed");
     }
     c->stream = c->own_stream;
-    if (cudaMalloc(&c->d_st, sizeof(DevState)) != cudaSuccess || cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&c->d_st, sizeof(DevState)) != cudaSuccess || cudaMalloc(&c->d_err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_bad, sizeof(long long)) != cudaSuccess) {
         oots_destroy(c);
         return fail(OOTS_E_NOMEM, "device state");
     }
@@ -672,9 +738,12 @@ int oots_destroy(oots_ctx *c)
     free_dev(c->d_xh);
     free_dev(c->d_N1);
     free_dev(c->d_N2);
+    free_dev(c->d_stage);
     void *p = c->d_st;
     free_dev(p);
     p = c->d_err;
+    free_dev(p);
+    p = c->d_bad;
     free_dev(p);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
@@ -712,6 +781,7 @@ int oots_set_grid(oots_ctx *c, int nx, int ny, int nz, double dx_cm)
     free_dev(c->d_xh);
     free_dev(c->d_N1);
     free_dev(c->d_N2);
+    free_dev(c->d_stage);
     c->nsrc_alloc = 0;
     c->nx = nx; c->ny = ny; c->nz = nz;
     c->dx = dx_cm;
@@ -752,15 +822,15 @@ int oots_set_density(oots_ctx *c, const double *n_H, double uniform_n)
         c->n_uniform = uniform_n;
         free_dev(c->d_n);
     } else {
-        for (long long i = 0; i < c->ncell; i++)
-            if (!(n_H[i] > 0) || !std::isfinite(n_H[i])) return fail(OOTS_E_INVAL, "density %g at cell %lld", n_H[i], i);
         if (!c->d_n && cudaMalloc(&c->d_n, (size_t)c->ncell * c->rsize) != cudaSuccess) {
             c->d_n = nullptr;
             cudaGetLastError();
             return fail(OOTS_E_NOMEM, "density array");
         }
-        int rc = to_real_upload(c, c->d_n, n_H, 0.0);
+        long long bad = -1;
+        int rc = to_real_upload(c, c->d_n, n_H, 0.0, 1, &bad);
         if (rc) return rc;
+        if (bad >= 0) return fail(OOTS_E_INVAL, "density %g at cell %lld", n_H[bad], bad);
         c->uniform_n = false;
     }
     drop_solo(c);
@@ -772,12 +842,13 @@ int oots_set_neutral_fraction(oots_ctx *c, const double *x, double uniform_x)
     if (int rc = check_ctx(c)) return rc;
     if (c->ncell == 0) return fail(OOTS_E_STATE, "no grid");
     if (!x && !(uniform_x >= 0.0 && uniform_x <= 1.0)) return fail(OOTS_E_INVAL, "neutral fraction %g outside [0,1]", uniform_x);
-    if (x)
-        for (long long i = 0; i < c->ncell; i++)
-            if (!(x[i] >= 0.0 && x[i] <= 1.0)) return fail(OOTS_E_INVAL, "neutral fraction %g at cell %lld", x[i], i);
     CU(cudaSetDevice(c->device));
     CU(cudaStreamSynchronize(c->stream));
-    return to_real_upload(c, c->d_x, x, uniform_x);
+    long long bad = -1;
+    int rc = to_real_upload(c, c->d_x, x, uniform_x, 0, &bad);
+    if (rc) return rc;
+    if (bad >= 0) return fail(OOTS_E_INVAL, "neutral fraction %g at cell %lld", x[bad], bad);
+    return OOTS_OK;
 }
 
 int oots_set_physics(oots_ctx *c, double alpha_B, double sigma0, double tau0, double T)
@@ -1009,6 +1080,7 @@ int oots_get_neutral_fraction(oots_ctx *c, double *out)
     if (!out) return fail(OOTS_E_INVAL, "out is NULL");
     if (c->ncell == 0) return fail(OOTS_E_STATE, "no grid");
     CU(cudaSetDevice(c->device));
+    CU(cudaStreamSynchronize(c->stream));
     return download_real(c, c->d_x, out);
 }
 
@@ -1019,6 +1091,7 @@ int oots_get_column_density(oots_ctx *c, int source, double *out)
     if (source < 0 || source >= (int)c->src.size()) return fail(OOTS_E_INVAL, "source %d", source);
     if (!c->d_N1 || source >= c->nsrc_alloc) return fail(OOTS_E_STATE, "no trace yet");
     CU(cudaSetDevice(c->device));
+    CU(cudaStreamSynchronize(c->stream));
     return download_real(c, (const char *)c->d_N1 + (size_t)source * c->ncell * c->rsize, out);
 }
 
@@ -1062,15 +1135,6 @@ int oots_set_time(oots_ctx *c, double t)
     if (rc) return rc;
     c->h_st.t = t;
     return push_state(c);
-}
-
-__global__ void convert_kernel(const void *src, int sd, void *dst, int dd, long long n)
-{
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double v = sd == 0 ? ((const double *)src)[i] : (double)((const float *)src)[i];
-    if (dd == 0) ((double *)dst)[i] = v;
-    else ((float *)dst)[i] = (float)v;
 }
 
 int oots_set_neutral_fraction_device(oots_ctx *c, const void *x_dev, int dtype)
@@ -1221,6 +1285,22 @@ int oots_batch_advance(oots_batch *b, const double *t_end_each, long long *nsub_
     if (nsub_out)
         for (size_t i = 0; i < b->ctxs.size(); i++) nsub_out[i] = b->ctxs[i]->h_st.nsub - n0[i];
     return OOTS_OK;
+}
+
+int oots_batch_run_substeps(oots_batch *b, long long n, const double *t_end_each)
+{
+    if (!b || !t_end_each || n < 0) return fail(OOTS_E_INVAL, "batch arguments");
+    for (size_t i = 0; i < b->ctxs.size(); i++) {
+        if (!std::isfinite(t_end_each[i])) return fail(OOTS_E_INVAL, "t_end %g of context %zu", t_end_each[i], i);
+        oots_ctx *c = b->ctxs[i];
+        int rc = pull_state(c);
+        if (rc) return rc;
+        c->h_st.t_end = t_end_each[i];
+        c->h_st.done = (t_end_each[i] > c->h_st.t) ? 0 : 1;
+        if ((rc = push_state(c))) return rc;
+    }
+    CU(cudaSetDevice(b->ctxs[0]->device));
+    return n > 0 ? b->L->graph_replay(b->stream, (int)n) : OOTS_OK;
 }
 
 int oots_batch_destroy(oots_batch *b)

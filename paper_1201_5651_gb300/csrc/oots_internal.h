@@ -73,6 +73,7 @@ template <typename Real> struct GridDev {
     Real qfac[MAX_SRC];       // Q / (4 pi dx^3); a plane source's flux F / dx
     int tab[MAX_SRC];         // -1 monochromatic, else table index
     unsigned char pcode[MAX_SRC];  // 0: vertex point source; 1 + 2*axis + back: plane source (qfac = F/dx)
+    float lnamp0[MAX_SRC];    // ln(qfac sigma0 dx): a source's largest rate per unit x is qfac sigma0 dx p / r2
     DevState *st;
 };
 

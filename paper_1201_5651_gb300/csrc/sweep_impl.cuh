@@ -743,6 +743,12 @@ sweep_kernel(SweepParams<Real> P)
     if (tid == 0 && atomicAdd(P.done, 1u) == gridDim.x - 1) *(volatile unsigned *)P.epoch = epoch;
 }
 
+} // namespace oots
+
+#include "sweep_tp.cuh"
+
+namespace oots {
+
 // ---------------------------------------------------------------------------
 // Launch wrappers
 // ---------------------------------------------------------------------------
@@ -780,6 +786,7 @@ static cudaError_t prepare_shape()
 template <typename Real>
 bool sweep_shape_ok(int shape)
 {
+    if (shape == SHAPE_TP8) return (int)sweep_tp_smem<Real, 8>() <= max_optin_smem() && sweep_shape_ok<Real>(4);
     size_t sm = 0;
 #define OOTS_SM(ID, TX, TY, TZ) if (shape == ID) sm = sweep_smem<Real, TX, TY, TZ>();
     OOTS_SHAPES(OOTS_SM)
@@ -792,6 +799,11 @@ int sweep_occupancy(int shape, int mode)
 {
     int nb = 0;
     cudaError_t e = cudaSuccess;
+    if (shape == SHAPE_TP8) {
+        if (mode == 1) return sweep_occupancy<Real>(4, 1);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_tp_kernel<Real, 8>, 64, sweep_tp_smem<Real, 8>());
+        return (e == cudaSuccess && nb > 0) ? nb : 1;
+    }
 #define OOTS_OCC(ID, TX, TY, TZ)                                                                      \
     if (shape == ID) {                                                                                \
         constexpr size_t sm = sweep_smem<Real, TX, TY, TZ>();                                         \
@@ -811,6 +823,11 @@ cudaError_t launch_sweep(const SweepParams<Real> &P, int shape, int mode, int nb
     long long nb = nblocks;
     if (nb > P.nitems) nb = P.nitems;
     if (nb < 1) nb = 1;
+    if (shape == SHAPE_TP8) {
+        if (mode == 1) return launch_sweep<Real>(P, 4, 1, nblocks, s);
+        sweep_tp_kernel<Real, 8><<<(int)nb, 64, sweep_tp_smem<Real, 8>(), s>>>(P);
+        return cudaGetLastError();
+    }
 #define OOTS_LAUNCH(ID, TX, TY, TZ)                                                         \
     if (shape == ID) {                                                                      \
         return mode == 0 ? launch_shape<Real, TX, TY, TZ, 0>(P, (int)nb, s)                 \
@@ -830,6 +847,11 @@ cudaError_t prepare_sweeps()
     e2 = prepare_shape<Real, TX, TY, TZ, 1>(); if (e2 != cudaSuccess) e = e2;
     OOTS_SHAPES(OOTS_PREP)
 #undef OOTS_PREP
+    if ((int)sweep_tp_smem<Real, 8>() <= max_optin_smem()) {
+        e2 = cudaFuncSetAttribute(sweep_tp_kernel<Real, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sweep_tp_smem<Real, 8>());
+        if (e2 != cudaSuccess) e = e2;
+    }
     return e;
 }
 

@@ -38,7 +38,7 @@ EXPORTS = [
     "oots_set_neutral_fraction_device", "oots_get_neutral_fraction_device", "oots_synchronize",
     "oots_batch_create", "oots_batch_advance", "oots_batch_destroy", "oots_set_tile_shape",
     "oots_tile_shape_info", "oots_debug_set", "oots_version", "oots_run_substeps", "oots_profile_substep",
-    "oots_trace_noalloc", "oots_add_plane_source",
+    "oots_trace_noalloc", "oots_add_plane_source", "oots_batch_run_substeps",
 ]
 KERNEL_KINDS = {1: "sweep1", 2: "ratedt", 3: "final0", 4: "half", 5: "sweep2", 6: "full", 7: "final1", 8: "implicit",
                 9: "half_general", 10: "full_general", 11: "plane_trace", 12: "plane_implicit"}
@@ -111,6 +111,7 @@ def load(build_if_missing: bool = True):
         "oots_batch_create": ([P(vp), P(vp), ip], ip),
         "oots_batch_advance": ([vp, P(dp), P(ctypes.c_longlong)], ip),
         "oots_batch_destroy": ([vp], ip),
+        "oots_batch_run_substeps": ([vp, ctypes.c_longlong, P(dp)], ip),
         "oots_set_tile_shape": ([vp, ip], ip),
         "oots_tile_shape_info": ([ip, P(ip)], ip),
         "oots_debug_set": ([vp, ip, ctypes.c_longlong], ip),
@@ -297,6 +298,13 @@ class Context:
         self._c(self.lib.oots_get_neutral_fraction(self.h, _dptr(out)))
         return out
 
+    def get_neutral_fraction_into(self, out: np.ndarray) -> np.ndarray:
+        """oots_get_neutral_fraction into a caller-owned contiguous float64 host array."""
+        if out.dtype != np.float64 or not out.flags.c_contiguous or out.size != int(np.prod(self.shape)):
+            raise ValueError("out must be a contiguous float64 array of one value per cell")
+        self._c(self.lib.oots_get_neutral_fraction(self.h, _dptr(out)))
+        return out
+
     def get_column_density(self, source: int = 0) -> np.ndarray:
         out = np.empty(self.shape, np.float64)
         self._c(self.lib.oots_get_column_density(self.h, int(source), _dptr(out)))
@@ -363,6 +371,12 @@ class Batch:
         ns = (ctypes.c_longlong * len(self.ctxs))()
         _check(self.lib.oots_batch_advance(self.h, te, ns))
         return list(ns)
+
+    def run_substeps(self, n: int, t_end_each: Sequence[float]):
+        """Enqueue exactly n substeps of every grid (asynchronous; pair with the
+        first context's synchronize())."""
+        te = (ctypes.c_double * len(self.ctxs))(*[float(t) for t in t_end_each])
+        _check(self.lib.oots_batch_run_substeps(self.h, int(n), te))
 
     def close(self):
         if self.h is not None:
