@@ -50,7 +50,7 @@ T_END_RUN = 10.0          # end of the advance the timed substeps belong to, in 
 
 WORKLOADS = {
     "multisource512_bb": dict(
-        t0=0.005, n_oct=8, k64=2,
+        t0=0.005, n_oct=8, k64=1,
         describe="512^3 lognormal n_H (mean 100, sigma_ln 1, P(k)~k^-3, seed 1205), 16 blackbody sources "
                  "(T 3e4-5e4 K, Q log-uniform 1e47-1e49 s^-1, random vertices, seed 1205), box 2 R_S(sum Q), "
                  "A3-dt02 (K4=1/4), t0 = 0.005 t_rec"),

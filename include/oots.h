@@ -231,6 +231,51 @@ int oots_get_neutral_fraction_device(oots_ctx *ctx, void *x_dev, int dtype);
 /* Block until the context's stream is idle; returns a pending device error. */
 int oots_synchronize(oots_ctx *ctx);
 
+/* ---- partitioned runs (one process per GPU) -------------------------------------------------- */
+
+/* The paper decomposes its domain and traces each source's rays outward from
+ * the source, passing columns between subdomains (Sect. 5).  Here a run over
+ * several GPUs splits the work of every substep two ways: each process
+ * traces only the sources whose bit is set in src_mask (bit s = source s;
+ * ~0 for all), and integrates, and takes the Eq. 4 minimum over, only the
+ * cells with z in [z0, z1) (z1 <= 0: to nz).  Every process keeps the whole
+ * state and all columns; the caller exchanges them between the phases below
+ * (a trace's columns of every source on every process's cells; the half-step
+ * and full-step states of every process's cells; the minimum of the dt
+ * values).  Point sources and the explicit schemes A2/A3 only.  The default
+ * partition (all sources, all cells) makes the phases one substep.
+ * Errors: E_INVAL (z-range), E_STATE (no grid). */
+int oots_set_partition(oots_ctx *ctx, unsigned long long src_mask, int z0, int z1);
+
+/* One phase of a substep on this context's partition, in the scheme's order:
+ *   OOTS_PH_TRACE1  trace x into the first columns (the partition's sources);
+ *   OOTS_PH_DT      Eq. 4 minimum over the partition's cells into *value (not
+ *                   capped by an end time; 1e300 when nothing limits it); it
+ *                   needs the first columns of every source on those cells;
+ *   OOTS_PH_STEP1   take the step *value (> 0): A3 the half step into
+ *                   x_half, A2 the whole step into x (time += *value);
+ *   OOTS_PH_TRACE2  (A3) trace x_half into the second columns;
+ *   OOTS_PH_FULL    (A3) the full step into x with the second columns of every
+ *                   source, time += the step.
+ * Each call finishes its work before it returns.  Errors: E_INVAL (phase out
+ * of order for the scheme, value NULL or dt not positive), E_UNSUPPORTED (A1
+ * or plane sources), E_DEVICE_TIMEOUT, E_CUDA. */
+#define OOTS_PH_TRACE1  0
+#define OOTS_PH_DT      1
+#define OOTS_PH_STEP1   2
+#define OOTS_PH_TRACE2  3
+#define OOTS_PH_FULL    4
+int oots_run_phase(oots_ctx *ctx, int phase, double *value);
+
+/* Device address and size in bytes of one of the context's arrays, for
+ * exchanges between processes (e.g. NCCL broadcasts into it): kind 0 the
+ * state x, 1 the half-step state x_half, 2 the first columns of source
+ * `source`, 3 its second columns; ncell values each, x-fastest, in the
+ * context's precision (double for OOTS_FP64, float for OOTS_MIXED).  The
+ * memory stays owned by the context and valid until its grid, sources or
+ * partition change.  Errors: E_INVAL, E_STATE. */
+int oots_array_device(oots_ctx *ctx, int kind, int source, void **ptr, unsigned long long *bytes);
+
 /* ---- batches ------------------------------------------------------------------------------- */
 
 /* Group n contexts of the same device and precision, each with its grid,

@@ -85,6 +85,8 @@ def _load():
         lib.or_long_char.restype = None
         lib.or_compute_dt.argtypes = [P, ctypes.POINTER(_Scheme), dp]
         lib.or_compute_dt.restype = ctypes.c_double
+        lib.or_crit_dt_range.argtypes = [P, ctypes.POINTER(_Scheme), dp, dp, ctypes.c_long, ctypes.c_long]
+        lib.or_crit_dt_range.restype = ctypes.c_double
         lib.or_snap.argtypes = [ctypes.c_double, ctypes.c_int]
         lib.or_snap.restype = ctypes.c_int
         _lib = lib
@@ -223,6 +225,14 @@ class Problem:
         x = np.ascontiguousarray(x, np.float64).reshape(self.nz, self.ny, self.nx)
         sc = _Scheme(int(scheme), float(K1), float(K3), float(K4), 0.0)
         return _load().or_compute_dt(ctypes.byref(self.st), ctypes.byref(sc), _ptr(x))
+
+    def crit_dt_range(self, x: np.ndarray, Nin: np.ndarray, lo: int, hi: int, scheme: int = 3, K1=0.0, K3=0.0,
+                      K4=0.0) -> float:
+        """Eq. 4 minimum over the cells [lo, hi) (flat indices) for x and entry columns Nin (nsrc, nz, ny, nx)."""
+        x = np.ascontiguousarray(x, np.float64).reshape(self.nz, self.ny, self.nx)
+        Nin = np.ascontiguousarray(Nin, np.float64)
+        sc = _Scheme(int(scheme), float(K1), float(K3), float(K4), 0.0)
+        return _load().or_crit_dt_range(ctypes.byref(self.st), ctypes.byref(sc), _ptr(x), _ptr(Nin), int(lo), int(hi))
 
     def run(self, x: np.ndarray, t: float, t_end: float, scheme: int = 3, max_steps: int = 10 ** 9,
             callback=None, **crit):

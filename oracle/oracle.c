@@ -860,13 +860,14 @@ void or_rates(const or_problem *p, const double *x, const double *Nin, double *F
     free(r);
 }
 
-/* Eq. 4 without the energy criterion: minimum over all cells (Sect. 2.2,
- * step 2) of K1 t_rec, K3 max(0.05, x)/|dx/dt|, K4/|dx/dt|. */
-static double crit_dt(const or_problem *p, const or_scheme *sc, const double *x, const double *xdot)
+/* Eq. 4 without the energy criterion: minimum over the cells with flat
+ * index in [lo, hi) (all cells for the scheme, Sect. 2.2 step 2) of K1 t_rec,
+ * K3 max(0.05, x)/|dx/dt|, K4/|dx/dt|. */
+static double crit_dt_range(const or_problem *p, const or_scheme *sc, const double *x, const double *xdot,
+                            long lo, long hi)
 {
-    long ncell = (long)p->nx * p->ny * p->nz;
     double dt = INFINITY;
-    for (long gi = 0; gi < ncell; gi++) {
+    for (long gi = lo; gi < hi; gi++) {
         if (sc->K1 > 0) {
             double v = sc->K1 / (p->alpha * p->nH[gi]);
             if (v < dt) dt = v;
@@ -885,6 +886,24 @@ static double crit_dt(const or_problem *p, const or_scheme *sc, const double *x,
             }
         }
     }
+    return dt;
+}
+
+static double crit_dt(const or_problem *p, const or_scheme *sc, const double *x, const double *xdot)
+{
+    return crit_dt_range(p, sc, x, xdot, 0, (long)p->nx * p->ny * p->nz);
+}
+
+/* The Eq. 4 minimum over the cells [lo, hi) for the state x and given entry
+ * columns Nin (nsrc x ncell): one process's share of the cells when the
+ * cells are split over processes (Sect. 5).  +inf when nothing limits it. */
+double or_crit_dt_range(const or_problem *p, const or_scheme *sc, const double *x, const double *Nin, long lo, long hi)
+{
+    long ncell = (long)p->nx * p->ny * p->nz;
+    double *xdot = (double *)malloc(sizeof(double) * ncell);
+    or_rates(p, x, Nin, NULL, xdot);
+    double dt = crit_dt_range(p, sc, x, xdot, lo < 0 ? 0 : lo, hi > ncell ? ncell : hi);
+    free(xdot);
     return dt;
 }
 

@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(256, 4) cell_kernel(const GridDev<Real> *grids
         const GridDev<Real> &G = grids[gi];
         DevState *st = G.st;
         const long long idx = base + threadIdx.x;
-        const bool mine = idx < total && idx >= offsets[gi] && (gi + 1 >= ngrid || idx < offsets[gi + 1]);
+        const bool mine = idx < total && idx >= offsets[gi] && (gi + 1 >= ngrid || idx < offsets[gi + 1]) &&
+                          idx - offsets[gi] >= G.cell_lo && idx - offsets[gi] < G.cell_hi;
         if (F32) {
             if (threadIdx.x == 0) {
                 const double d = st->dt;
@@ -395,18 +396,45 @@ __device__ __forceinline__ float src_lnamp(const GridDev<Real> &G, const DevTabl
     return G.lnamp0[s] + lnp - __logf(r2);
 }
 
+// The entry column beyond which source s cannot reach the threshold e^lnthr at
+// any cell: r2 >= 3/4, so amp <= e^lnthr whenever ln P/Q <= lnthr - ln(qfac
+// sigma0 dx) + ln(3/4).  Monochromatic: ln P/Q = -sigma0 N.  Tabulated: the
+// bound lnp_upper reads the node one interval below N, so N at or above the
+// node after the first node below the target qualifies.  +inf: never.
+template <typename Real>
+__device__ Real negligible_column(const GridDev<Real> &G, const DevTable<Real> *tabs, int s, float lnthr)
+{
+    const float target = lnthr - G.lnamp0[s] + -0.2876821f;          // ln(3/4)
+    if (!(target > -1e30f)) return RealLimits<Real>::inf();        // lnthr = -inf: keep everything
+    if (target >= 0.0f) return Real(0);                            // never above the threshold
+    if (G.tab[s] < 0) return Real(-target) / G.sigma0;
+    const DevTable<Real> &T = tabs[G.tab[s]];
+    // first node with L <= target (L falls with the node index)
+    int lo = 0, hi = T.K;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (float(T.L[mid]) <= target) hi = mid; else lo = mid + 1;
+    }
+    if (lo + 1 >= T.K) return T.Nhi;                                // beyond the table P = 0
+    return T.Nnode[lo + 1];
+}
+
 // Rate parameters of the sources whose bound exceeds e^lnthr, into
 // r[0 .. NK-1] (indices fixed at compile time, so r stays in registers).
 // Returns how many there are; NK + 1 when there are more than NK.
+// nstar (may be null): per source a column beyond which the source is left
+// out without forming its bound.
 template <typename Real, int NK>
 __device__ __forceinline__ int gather_rates(const GridDev<Real> &G, const Real *Ncol, const DevTable<Real> *tabs,
-                                            int X, int Y, int Z, long long g, Real n, float lnthr, SrcRate<Real> *r)
+                                            int X, int Y, int Z, long long g, Real n, float lnthr, SrcRate<Real> *r,
+                                            const Real *nstar)
 {
     int cnt = 0;
     for (int s = 0; s < G.nsrc; s++) {
+        const Real N = Ncol[(long long)s * G.ncell + g];
+        if (nstar && N >= nstar[s]) continue;
         int i, j, k;
         const float r2 = src_cell(G, s, X, Y, Z, i, j, k);
-        const Real N = Ncol[(long long)s * G.ncell + g];
         if (!(src_lnamp(G, tabs, s, r2, N) > lnthr)) continue;
         if (cnt == NK) return NK + 1;
         SrcRate<Real> t;
@@ -458,21 +486,22 @@ __device__ __forceinline__ bool closed_form_from_F(Real c, Real x0, Real h, Real
 
 // Per-cell passes of grids with several sources.
 //
-// RATEDT (Eq. 4 minimum over cells) first bounds every source's rate at the
-// cell, then forms the exact |dx/dt| only where the cell can set the step: a
-// cell whose upper bound of |dx/dt| gives a criterion above the hint H
-// (four times the previous substep's step) cannot be the minimum if the
-// minimum is below H, and sources whose bound times H is below a thousandth
-// of the rounding are left out of the sum (they change the limiting |dx/dt|
-// by far less than its rounding).  A second, verifying launch (verify = 1)
-// recomputes every cell without hint when the minimum came out above H; it
-// returns at once otherwise.  RATEDT caches F, F' (NaN where it skipped the
-// cell) and the sum of the sources' bounds for the step that follows on the
-// same columns (A3's half step, A2's full step).  That step settles
-// photon-free and slow cells from the cache alone; A3's full step (new
-// columns) and the cells the cache does not settle select their sources for
-// the step and run the closed forms on them.  The rest go to the general pass.
-// The kernel walks 256-cell chunks with a stride of the grid size.
+// RATEDT (Eq. 4 minimum over cells) bounds every source's rate at the cell
+// against a hint H of the step (four times the last substep's) and forms the
+// exact F and F' from the sources whose bound times H exceeds a thousandth
+// of the rounding; a cell that no source reaches so is photon-free within H
+// (F = F' = 0) and only recombines.  Left-out sources change the limiting
+// |dx/dt| by far less than its rounding as long as the step comes out below
+// H; a second, verifying launch (verify = 1) recomputes every cell without
+// hint when it did not, and returns at once otherwise.  Per source, a column
+// beyond which it cannot reach the threshold anywhere (nstar, set by the
+// finalize kernel once per substep) skips even the bound.  RATEDT caches F,
+// F' and the sum of the bounds for the step that follows on the same columns
+// (A3's half step, A2's full step), which settles photon-free and slow cells
+// from the cache alone.  A3's full step (new columns) and the cells the cache
+// does not settle select their sources for the step and run the closed forms
+// on them; the rest go to the general pass.  The kernel walks 256-cell
+// chunks with a stride of the grid size.
 template <typename Real, int OP>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_kernel(const GridDev<Real> *grids, int ngrid,
                                                          const long long *offsets, long long total,
@@ -491,7 +520,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_ker
             int any = 0;
             for (int q = 0; q < ngrid && !any; q++) {
                 const DevState *sq = grids[q].st;
-                const double d = sq->dt;
+                const double d = sq->dt_last;
                 const unsigned long long b = sq->dt_bits;
                 if (sq->done || !(d > 0.0)) continue;            // no hint was used
                 any = b == 0xffffffffffffffffull || __longlong_as_double((long long)b) > 4.0 * d;
@@ -519,8 +548,9 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_ker
             s_h = h;
             s_skip = 0;
             if (OP == OP_RATEDT) {
-                // st->dt still holds the previous substep's step here
-                double hint = d > 0.0 ? 4.0 * d : __longlong_as_double(0x7ff0000000000000ll);
+                // the last substep's step (st->dt of this substep is not chosen yet)
+                const double dl = st->dt_last;
+                double hint = dl > 0.0 ? 4.0 * dl : __longlong_as_double(0x7ff0000000000000ll);
                 if (verify) {
                     // a minimum at or below the hint stands: every cell the first pass
                     // skipped asks for more.  (Other blocks of this pass may have lowered
@@ -528,7 +558,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_ker
                     const unsigned long long b = st->dt_bits;
                     const double mn = b == 0xffffffffffffffffull ? __longlong_as_double(0x7ff0000000000000ll)
                                                                 : __longlong_as_double((long long)b);
-                    if (!(d > 0.0) || mn <= hint) s_skip = 1;
+                    if (!(dl > 0.0) || mn <= hint) s_skip = 1;
                     hint = __longlong_as_double(0x7ff0000000000000ll);
                 }
                 s_hint = hint;
@@ -544,7 +574,8 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_ker
         __syncthreads();
         if (s_skip) { __syncthreads(); continue; }
         const long long idx = base + threadIdx.x;
-        const bool mine = idx < total && idx >= offsets[gi] && (gi + 1 >= ngrid || idx < offsets[gi + 1]);
+        const bool mine = idx < total && idx >= offsets[gi] && (gi + 1 >= ngrid || idx < offsets[gi + 1]) &&
+                          idx - offsets[gi] >= G.cell_lo && idx - offsets[gi] < G.cell_hi;
         const bool stepping = s_h > 0.0;
         const bool active = mine && (OP == OP_RATEDT ? !st->done : stepping);
         double dtmin = __longlong_as_double(0x7ff0000000000000ll);
@@ -562,27 +593,28 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_ker
             const Real c = G.alpha * n;
             const float lnthr = s_lnthr;
             if (OP == OP_RATEDT) {
-                // Eq. 4 with T fixed: K1 t_rec, K3 max(0.05, x)/|dx/dt|, K4/|dx/dt|
+                // Eq. 4 with T fixed: K1 t_rec, K3 max(0.05, x)/|dx/dt|, K4/|dx/dt|.
+                // The sources that can matter within the hint, by their bounds; a
+                // cell that none of them lights within the hint is photon-free
+                // (F = F' = 0) and only recombines.
+                const Real *nst = (G.nstar && !verify) ? G.nstar : nullptr;
                 float ampsum = 0.0f;
                 for (int s = 0; s < G.nsrc; s++) {
+                    const Real N = G.N1[(long long)s * G.ncell + g];
+                    if (nst && N >= nst[s]) continue;
                     int i, j, k;
                     const float r2 = src_cell(G, s, X, Y, Z, i, j, k);
-                    ampsum += __expf(src_lnamp(G, tabs, s, r2, G.N1[(long long)s * G.ncell + g]));
+                    const float la = src_lnamp(G, tabs, s, r2, N);
+                    if (la > lnthr) ampsum += __expf(la);
                 }
-                // |dx/dt| <= F + c (1-x)^2 with F <= x0 sum(amp): the smallest step the cell could ask for
-                const double xdu = double(ampsum) * double(x0) * 1.0001 + double(c) * double(Real(1) - x0) * double(Real(1) - x0);
-                double lowest = __longlong_as_double(0x7ff0000000000000ll);
-                if (xdu > 0.0) {
-                    if (st->K3 > 0) lowest = fmin(lowest, st->K3 * fmax(0.05, double(x0)) / xdu);
-                    if (st->K4 > 0) lowest = fmin(lowest, st->K4 / xdu);
-                }
-                const bool exact = lowest < s_hint;
+                const bool exact = !(s_hint < 1e300) || double(ampsum) * s_hint > 1e-3 * double(RealLimits<Real>::eps());
                 Real F = Real(0), dF = Real(0);
                 if (exact) {
                     for (int s = 0; s < G.nsrc; s++) {
+                        const Real N = G.N1[(long long)s * G.ncell + g];
+                        if (nst && N >= nst[s]) continue;
                         int i, j, k;
                         const float r2 = src_cell(G, s, X, Y, Z, i, j, k);
-                        const Real N = G.N1[(long long)s * G.ncell + g];
                         if (!(src_lnamp(G, tabs, s, r2, N) > lnthr)) continue;
                         SrcRate<Real> t;
                         src_rate<Real>(t, G.qfac[s], G.tab[s], G.sigma0, G.dx, n, G.pcode[s] != 0, i, j, k, N, tabs);
@@ -595,21 +627,21 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_ker
                     }
                 }
                 if (rcache) {
-                    rcache[idx] = exact ? F : __int_as_float(0x7fc00000);
+                    rcache[idx] = F;
                     rcache[total + idx] = dF;
                     rcache[2 * total + idx] = Real(ampsum);
                 }
                 if (F32) {
                     if (s_f[1] > 0.0f) dtmin_f = fminf(dtmin_f, s_f[1] / (float(G.alpha) * float(n)));
                     const float xd = fabsf(float(-F + c * (Real(1) - x0) * (Real(1) - x0)));
-                    if (exact && xd > 0.0f) {
+                    if (xd > 0.0f) {
                         if (s_f[2] > 0.0f) dtmin_f = fminf(dtmin_f, s_f[2] * fmaxf(0.05f, float(x0)) / xd);
                         if (s_f[3] > 0.0f) dtmin_f = fminf(dtmin_f, s_f[3] / xd);
                     }
                 } else {
                     if (st->K1 > 0) dtmin = fmin(dtmin, st->K1 / (double(G.alpha) * double(n)));
                     const double xd = fabs((double)(-F + c * (Real(1) - x0) * (Real(1) - x0)));
-                    if (exact && xd > 0) {
+                    if (xd > 0) {
                         if (st->K3 > 0) dtmin = fmin(dtmin, st->K3 * fmax(0.05, (double)x0) / xd);
                         if (st->K4 > 0) dtmin = fmin(dtmin, st->K4 / xd);
                     }
@@ -645,7 +677,8 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_ker
                 if (!done) {
                     SrcRate<Real> r[NACT];
                     const Real *Ncol = (OP == OP_FULL2) ? G.N2 : G.N1;
-                    const int na = gather_rates<Real, NACT>(G, Ncol, tabs, X, Y, Z, g, n, lnthr, r);
+                    const Real *nst = G.nstar ? G.nstar + (OP == OP_HALF ? 1 : 2) * MAX_SRC : nullptr;
+                    const int na = gather_rates<Real, NACT>(G, Ncol, tabs, X, Y, Z, g, n, lnthr, r, nst);
                     if (na <= NACT) {
                         CellODE<Real> C;
                         C.ns = na; C.c = c; C.b0 = Real(0); C.r = r; C.tabs = tabs;
@@ -758,7 +791,8 @@ cell_multi_general_kernel(const GridDev<Real> *grids, int ngrid, const long long
         IntResult<Real> R;
         Real F0, dF0, f0;
         SrcRate<Real> r[NACT_GEN];
-        const int na = gather_rates<Real, NACT_GEN>(G, Ncol, tabs, X, Y, Z, g, n, lnthr, r);
+        const Real *nst = G.nstar ? G.nstar + (OP == OP_HALF ? 1 : 2) * MAX_SRC : nullptr;
+        const int na = gather_rates<Real, NACT_GEN>(G, Ncol, tabs, X, Y, Z, g, n, lnthr, r, nst);
         if (na <= NACT_GEN) {
             CellODE<Real> C;
             C.ns = na; C.c = G.alpha * n; C.b0 = Real(0); C.r = r; C.tabs = tabs;
@@ -806,7 +840,8 @@ cell_multi_general_kernel(const GridDev<Real> *grids, int ngrid, const long long
 // stage 0: choose dt (Eq. 4 minimum or fixed, capped at t_end - t) and reset the step budget
 // stage 1: close the substep (t += dt, totals, done flag)
 template <typename Real>
-__global__ void finalize_kernel(const GridDev<Real> *grids, int ngrid, int stage, unsigned *qcount)
+__global__ void finalize_kernel(const GridDev<Real> *grids, int ngrid, int stage, unsigned *qcount,
+                                const DevTable<Real> *tabs)
 {
     const int gi = blockIdx.x * blockDim.x + threadIdx.x;
     if (stage == 0 && gi == 0) { qcount[0] = 0u; qcount[1] = 0u; qcount[2] = 0u; qcount[3] = 0u; }
@@ -823,7 +858,17 @@ __global__ void finalize_kernel(const GridDev<Real> *grids, int ngrid, int stage
             if (!(dt > 0.0)) { dt = 0.0; st->done = 1; }
         }
         st->dt = dt;
+        if (dt > 0.0) st->dt_last = dt;
         st->dt_bits = 0xffffffffffffffffull;
+        const GridDev<Real> &G = grids[gi];
+        if (G.nstar && dt > 0.0) {
+            // thresholds of the next dt pass (hint 4 dt), the half step and the full step
+            for (int s = 0; s < G.nsrc; s++) {
+                G.nstar[s] = negligible_column<Real>(G, tabs, s, lnthr_step<Real>(4.0 * dt));
+                G.nstar[MAX_SRC + s] = negligible_column<Real>(G, tabs, s, lnthr_step<Real>(0.5 * dt));
+                G.nstar[2 * MAX_SRC + s] = negligible_column<Real>(G, tabs, s, lnthr_step<Real>(dt));
+            }
+        }
         st->bud_step[0] = st->sumQ * dt;
         st->bud_step[1] = st->bud_step[2] = st->bud_step[3] = 0.0;
     } else {
@@ -901,9 +946,10 @@ int cell_general_occupancy(int nsmax)
 }
 
 template <typename Real>
-cudaError_t launch_finalize(const GridDev<Real> *grids, int ngrid, int stage, unsigned *qcount, cudaStream_t s)
+cudaError_t launch_finalize(const GridDev<Real> *grids, int ngrid, int stage, unsigned *qcount,
+                            const DevTable<Real> *tabs, cudaStream_t s)
 {
-    finalize_kernel<Real><<<(ngrid + 63) / 64, 64, 0, s>>>(grids, ngrid, stage, qcount);
+    finalize_kernel<Real><<<(ngrid + 63) / 64, 64, 0, s>>>(grids, ngrid, stage, qcount, tabs);
     return cudaGetLastError();
 }
 
@@ -917,7 +963,9 @@ template size_t queue_record_bytes<double>();
 template size_t queue_record_bytes<float>();
 template int cell_general_occupancy<double>(int);
 template int cell_general_occupancy<float>(int);
-template cudaError_t launch_finalize<double>(const GridDev<double> *, int, int, unsigned *, cudaStream_t);
-template cudaError_t launch_finalize<float>(const GridDev<float> *, int, int, unsigned *, cudaStream_t);
+template cudaError_t launch_finalize<double>(const GridDev<double> *, int, int, unsigned *, const DevTable<double> *,
+                                             cudaStream_t);
+template cudaError_t launch_finalize<float>(const GridDev<float> *, int, int, unsigned *, const DevTable<float> *,
+                                            cudaStream_t);
 
 } // namespace oots

@@ -80,6 +80,9 @@ template <> struct ColT<double> {
     static OOTS_HD __forceinline__ double addc(double a, double b) { return a + b; }
     static OOTS_HD __forceinline__ double to_real(double a) { return a; }
     static OOTS_HD __forceinline__ double sub_r(double a, double b) { return a - b; }
+    static OOTS_HD __forceinline__ double make(double hi, double) { return hi; }
+    static OOTS_HD __forceinline__ double hi(double a) { return a; }
+    static OOTS_HD __forceinline__ double lo(double) { return 0.0; }
 };
 template <> struct ColT<float> {
     typedef ff type;
@@ -91,6 +94,9 @@ template <> struct ColT<float> {
     static OOTS_HD __forceinline__ float to_real(ff a) { return a.hi + a.lo; }
     // a - b rounded to one float (exact high-part difference for close columns)
     static OOTS_HD __forceinline__ float sub_r(ff a, ff b) { return (a.hi - b.hi) + (a.lo - b.lo); }
+    static OOTS_HD __forceinline__ ff make(float hi, float lo) { return ff{hi, lo}; }
+    static OOTS_HD __forceinline__ float hi(ff a) { return a.hi; }
+    static OOTS_HD __forceinline__ float lo(ff a) { return a.lo; }
 };
 
 // ---------------------------------------------------------------------------

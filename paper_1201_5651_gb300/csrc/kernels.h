@@ -38,6 +38,8 @@ template <typename Real> struct SweepParams {
     unsigned long long *faces;         // per tile 3 faces x FMAX cells x tagged words (zeroed once)
     const DevTable<Real> *tabs;
     int *err;                          // sticky device error
+    Real *tpfaces;                     // throughput kernel: per tile 3 faces x tp_face_comps x 64 values
+    unsigned *tpflags;                 // throughput kernel: per tile the epoch of the launch that finished it
     long long spin_limit;              // bounded wait on upstream tiles
     long long skip_publish;            // tile that never writes its faces (fault-injection test), -1: none
     int chunk;                         // planes per hand-off chunk (<= 0: 4)
@@ -45,6 +47,9 @@ template <typename Real> struct SweepParams {
 
 // tagged 8-byte words per published face cell (mixed path 3, FP64 path 4)
 template <typename Real> constexpr int face_words() { return sizeof(Real) == 4 ? 3 : 4; }
+// values per face cell the throughput kernel publishes: the column (float-float
+// hi and lo in the mixed path, one double in FP64) and the weight factor
+template <typename Real> __host__ __device__ constexpr int tp_face_comps() { return sizeof(Real) == 4 ? 3 : 2; }
 
 template <typename Real> cudaError_t prepare_sweeps();
 template <typename Real> int sweep_occupancy(int shape, int mode);   // resident CTAs per SM
@@ -80,6 +85,7 @@ template <typename Real> size_t queue_record_bytes();
 template <typename Real> int cell_general_occupancy(int nsmax);
 // stage 0 also clears the queue lengths and the general passes' head counters
 template <typename Real>
-cudaError_t launch_finalize(const GridDev<Real> *grids, int ngrid, int stage, unsigned *qcount, cudaStream_t s);
+cudaError_t launch_finalize(const GridDev<Real> *grids, int ngrid, int stage, unsigned *qcount,
+                            const DevTable<Real> *tabs, cudaStream_t s);
 
 } // namespace oots

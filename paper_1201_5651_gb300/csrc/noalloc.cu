@@ -151,6 +151,8 @@ int trace_noalloc(DevSetup &S, int nx, int ny, int nz, double dx, const void *n_
     memset(&G, 0, sizeof(G));
     G.nx = nx; G.ny = ny; G.nz = nz;
     G.ncell = (long long)nx * ny * nz;
+    G.cell_lo = 0;
+    G.cell_hi = G.ncell;
     G.dx = Real(dx);
     G.sigma0 = Real(sigma0);
     G.tau0 = Real(tau0);
@@ -185,6 +187,8 @@ int trace_noalloc(DevSetup &S, int nx, int ny, int nz, double dx, const void *n_
     P.done = (unsigned *)(sc + kOffTicket) + 1;
     P.epoch = (unsigned *)(sc + kOffEpoch);
     P.faces = faces;
+    P.tpfaces = nullptr;
+    P.tpflags = nullptr;
     P.tabs = nullptr;
     P.err = (int *)(sc + kOffErr);
     P.spin_limit = 1ll << 22;

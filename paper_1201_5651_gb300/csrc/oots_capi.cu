@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -89,6 +90,9 @@ struct LaunchSetBase {
     virtual int substep(cudaStream_t s, bool fixed_dt) = 0;
     virtual int trace_for_dt(cudaStream_t s) = 0;
     virtual int graph_replay(cudaStream_t s, int n) = 0;
+    // one phase of a substep, eagerly (partitioned runs): 0 trace x, 1 dt pass,
+    // 2 choose dt and half step (A3; A2: full step), 3 trace x_half, 4 full step (A3)
+    virtual int phase(cudaStream_t s, int ph, bool use_cache) = 0;
 };
 
 struct oots_ctx {
@@ -115,6 +119,9 @@ struct oots_ctx {
     DevState *d_st = nullptr;
     int *d_err = nullptr;
     DevState h_st;
+    unsigned long long part_src = ~0ull;   // partition: sources this context traces (bit s)
+    int part_z0 = 0, part_z1 = 0;          // partition: z-range of the cells it updates (z1 <= 0: all)
+    bool phase_dt = false;                 // the dt phase ran on the current columns
     LaunchSetBase *solo = nullptr;
     bool dirty = true;      // sources / grid / shape / scheme changed since the launch set was built
     int nsm = 0;
@@ -144,6 +151,8 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     long long ntiles = 0;
     unsigned *d_sync = nullptr;        // [0] ticket, [1] done (zeroed per sweep), [16] epoch (persistent)
     unsigned long long *d_faces = nullptr;
+    Real *d_tpfaces = nullptr;         // throughput sweep: untagged faces, and a flag per tile
+    unsigned *d_tpflags = nullptr;
     PlaneJob *d_pjobs = nullptr;       // plane-parallel sources
     int npjobs = 0, nrow0 = 0;         // jobs; of them, rows along x (first in the array)
     long long plane_threads = 0, threads0 = 0;
@@ -154,6 +163,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     unsigned *d_queue = nullptr;       // cells left to the general pass (one entry per cell at most)
     Real *d_qrec = nullptr;            // their closed-form results (single-source launch sets)
     Real *d_rcache = nullptr;          // per cell: transmitted fraction, F(x0), F'(x0) from the dt pass
+    Real *d_nstar = nullptr;           // per grid 3 x MAX_SRC negligible-column thresholds (several sources)
     unsigned *d_qcount = nullptr;      // queue lengths of the half and full integrations
     int gen_blocks = 1;                // grid of the general pass
     int nblocks0 = 1, nblocks1 = 1;
@@ -174,6 +184,8 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         cudaFree(d_items);
         cudaFree(d_sync);
         cudaFree(d_faces);
+        cudaFree(d_tpfaces);
+        cudaFree(d_tpflags);
         cudaFree(d_pjobs);
         cudaFree(d_tabs);
         for (void *p : tabmem) cudaFree(p);
@@ -181,6 +193,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         cudaFree(d_queue);
         cudaFree(d_qrec);
         cudaFree(d_rcache);
+        cudaFree(d_nstar);
         cudaFree(d_qcount);
     }
 
@@ -241,6 +254,12 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
             memset(&G, 0, sizeof(G));
             G.nx = c->nx; G.ny = c->ny; G.nz = c->nz;
             G.ncell = c->ncell;
+            {
+                const long long plane = (long long)c->nx * c->ny;
+                const int z1 = c->part_z1 > 0 ? std::min(c->part_z1, c->nz) : c->nz;
+                G.cell_lo = plane * std::max(c->part_z0, 0);
+                G.cell_hi = plane * z1;
+            }
             G.dx = Real(c->dx);
             G.sigma0 = Real(c->sigma0);
             G.tau0 = Real(c->tau0);
@@ -271,6 +290,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
                     tabs.push_back(T);
                 }
                 const int n3[3] = {c->nx, c->ny, c->nz};
+                if (s < 64 && !((c->part_src >> s) & 1ull)) continue;   // traced by another process
                 if (S.pcode) {
                     PlaneJob P;
                     memset(&P, 0, sizeof(P));
@@ -326,6 +346,14 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         });
 
         CU(cudaSetDevice(device));
+        if (nsmax > 1) {
+            // no threshold until the first step sets them (+inf: every source is looked at)
+            const size_t nn = grids.size() * 3 * MAX_SRC;
+            std::vector<Real> inf(nn, std::numeric_limits<Real>::infinity());
+            CU(cudaMalloc(&d_nstar, nn * sizeof(Real)));
+            CU(cudaMemcpy(d_nstar, inf.data(), nn * sizeof(Real), cudaMemcpyHostToDevice));
+            for (size_t g = 0; g < grids.size(); g++) grids[g].nstar = d_nstar + g * 3 * MAX_SRC;
+        }
         CU(cudaMalloc(&d_grids, grids.size() * sizeof(GridDev<Real>)));
         CU(cudaMemcpy(d_grids, grids.data(), grids.size() * sizeof(GridDev<Real>), cudaMemcpyHostToDevice));
         CU(cudaMalloc(&d_offsets, offs.size() * sizeof(long long)));
@@ -343,10 +371,20 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
             CU(cudaMemcpy(d_items, items.data(), items.size() * sizeof(TileItem), cudaMemcpyHostToDevice));
             CU(cudaMalloc(&d_sync, 128));
             CU(cudaMemset(d_sync, 0, 128));
-            // faces start with epoch 0 in every word; launches use epochs 1, 2, ...
-            const size_t fbytes = (size_t)ntiles * 3 * FMAX * face_words<Real>() * sizeof(unsigned long long);
-            CU(cudaMalloc(&d_faces, fbytes));
-            CU(cudaMemset(d_faces, 0, fbytes));
+            // faces start with epoch 0 in every word (flags at 0); launches use epochs 1, 2, ...
+            // The pipelined kernel publishes tagged words; the throughput kernel
+            // (shape 7) plain values and a flag per tile; A1 runs the pipelined
+            // kernel on shape 7's tiles.
+            if (shape != SHAPE_TP8 || scheme == OOTS_A1) {
+                const size_t fbytes = (size_t)ntiles * 3 * FMAX * face_words<Real>() * sizeof(unsigned long long);
+                CU(cudaMalloc(&d_faces, fbytes));
+                CU(cudaMemset(d_faces, 0, fbytes));
+            }
+            if (shape == SHAPE_TP8) {
+                CU(cudaMalloc(&d_tpfaces, (size_t)ntiles * 3 * FMAX * tp_face_comps<Real>() * sizeof(Real)));
+                CU(cudaMalloc(&d_tpflags, (size_t)ntiles * sizeof(unsigned)));
+                CU(cudaMemset(d_tpflags, 0, (size_t)ntiles * sizeof(unsigned)));
+            }
         }
         if (!pjobs.empty()) {
             // rows along x first (their trace kernel differs), then the rest
@@ -386,6 +424,8 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         P.done = d_sync + 1;
         P.epoch = d_sync + 16;
         P.faces = d_faces;
+        P.tpfaces = d_tpfaces;
+        P.tpflags = d_tpflags;
         P.tabs = d_tabs;
         P.err = d_err;
         P.spin_limit = spin_limit;
@@ -431,7 +471,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     int fin(cudaStream_t s, int stage)
     {
         if (prof) prof->mark(0);
-        CU(launch_finalize<Real>(d_grids, (int)ctxs.size(), stage, d_qcount, s));
+        CU(launch_finalize<Real>(d_grids, (int)ctxs.size(), stage, d_qcount, d_tabs, s));
         if (prof) prof->mark(stage == 0 ? OOTS_K_FINAL0 : OOTS_K_FINAL1);
         return OOTS_OK;
     }
@@ -464,6 +504,28 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
             if ((rc = cell(s, OP_FULL1, !fixed_dt))) return rc;
         }
         return fin(s, 1);
+    }
+
+    int phase(cudaStream_t s, int ph, bool use_cache) override
+    {
+        switch (ph) {
+        case 0: return sweep(s, 0, 0);
+        case 1: return cell(s, OP_RATEDT);
+        case 2: {
+            int rc = fin(s, 0);
+            if (rc) return rc;
+            if (scheme == OOTS_A3) return cell(s, OP_HALF, use_cache);
+            if ((rc = cell(s, OP_FULL1, use_cache))) return rc;
+            return fin(s, 1);
+        }
+        case 3: return sweep(s, 1, 0);
+        case 4: {
+            int rc = cell(s, OP_FULL2);
+            if (rc) return rc;
+            return fin(s, 1);
+        }
+        }
+        return fail(OOTS_E_INVAL, "phase %d", ph);
     }
 
     int trace_for_dt(cudaStream_t s) override
@@ -1201,6 +1263,90 @@ int oots_debug_set(oots_ctx *c, int key, long long value)
         return fail(OOTS_E_INVAL, "debug key %d", key);
     }
     drop_solo(c);
+    return OOTS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// partitioned runs (one process per GPU)
+// ---------------------------------------------------------------------------
+int oots_set_partition(oots_ctx *c, unsigned long long src_mask, int z0, int z1)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (c->ncell == 0) return fail(OOTS_E_STATE, "no grid");
+    if (z0 < 0 || z0 > c->nz || (z1 > 0 && z1 < z0)) return fail(OOTS_E_INVAL, "z-range [%d, %d)", z0, z1);
+    c->part_src = src_mask;
+    c->part_z0 = z0;
+    c->part_z1 = z1;
+    c->phase_dt = false;
+    drop_solo(c);
+    return OOTS_OK;
+}
+
+int oots_run_phase(oots_ctx *c, int phase, double *value)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (phase < OOTS_PH_TRACE1 || phase > OOTS_PH_FULL) return fail(OOTS_E_INVAL, "phase %d", phase);
+    if (c->batched) return fail(OOTS_E_STATE, "context is part of a batch");
+    if (c->scheme == OOTS_A1) return fail(OOTS_E_UNSUPPORTED, "phases run the explicit schemes A2 and A3");
+    for (auto &S : c->src)
+        if (S.pcode) return fail(OOTS_E_UNSUPPORTED, "phases take point sources only");
+    if ((phase == OOTS_PH_STEP1 || phase == OOTS_PH_DT) && !value) return fail(OOTS_E_INVAL, "value is NULL");
+    if (phase == OOTS_PH_FULL && c->scheme != OOTS_A3) return fail(OOTS_E_INVAL, "A2 completes in OOTS_PH_STEP1");
+    if (phase == OOTS_PH_TRACE2 && c->scheme != OOTS_A3) return fail(OOTS_E_INVAL, "A2 has one trace");
+    int rc = prepare(c);
+    if (rc) return rc;
+    CU(cudaSetDevice(c->device));
+    if ((rc = pull_state(c))) return rc;
+    if (phase == OOTS_PH_DT) {
+        c->h_st.dt_bits = 0xffffffffffffffffull;
+        c->h_st.done = 0;
+    } else if (phase == OOTS_PH_STEP1) {
+        const double dt = *value;
+        if (!(dt > 0) || !std::isfinite(dt)) return fail(OOTS_E_INVAL, "dt %g", dt);
+        c->h_st.dt_fixed = dt;
+        c->h_st.t_end = c->h_st.t + dt;
+        c->h_st.done = 0;
+    } else {
+        c->h_st.done = 0;
+        if (!(c->h_st.t_end > c->h_st.t)) c->h_st.t_end = c->h_st.t + 1e300;
+    }
+    if ((rc = push_state(c))) return rc;
+    const bool use_cache = phase == OOTS_PH_STEP1 && c->phase_dt;
+    if ((rc = c->solo->phase(c->stream, phase, use_cache))) return rc;
+    if ((rc = check_device_error(c))) return rc;
+    if ((rc = pull_state(c))) return rc;
+    if (phase == OOTS_PH_TRACE1) c->phase_dt = false;
+    if (phase == OOTS_PH_DT) {
+        *value = c->h_st.dt_bits == 0xffffffffffffffffull ? 1e300 : *(double *)&c->h_st.dt_bits;
+        c->phase_dt = true;
+    }
+    if (phase == OOTS_PH_STEP1) c->phase_dt = false;
+    if ((phase == OOTS_PH_STEP1 && c->scheme == OOTS_A2) || phase == OOTS_PH_FULL) {
+        c->h_st.dt_fixed = c->crit.dt_fixed;
+        return push_state(c);
+    }
+    return OOTS_OK;
+}
+
+int oots_array_device(oots_ctx *c, int kind, int source, void **ptr, unsigned long long *bytes)
+{
+    if (int rc = check_ctx(c)) return rc;
+    if (!ptr) return fail(OOTS_E_INVAL, "ptr is NULL");
+    if (c->ncell == 0) return fail(OOTS_E_STATE, "no grid");
+    const size_t nb = (size_t)c->ncell * c->rsize;
+    char *base = nullptr;
+    if (kind == 0) base = (char *)c->d_x;
+    else if (kind == 1) base = (char *)c->d_xh;
+    else if (kind == 2 || kind == 3) {
+        if (source < 0 || source >= (int)c->src.size()) return fail(OOTS_E_INVAL, "source %d", source);
+        int rc = prepare(c);                 // the column arrays exist once the context is prepared
+        if (rc) return rc;
+        base = (char *)(kind == 2 ? c->d_N1 : c->d_N2) + (size_t)source * nb;
+    } else {
+        return fail(OOTS_E_INVAL, "array kind %d", kind);
+    }
+    *ptr = base;
+    if (bytes) *bytes = nb;
     return OOTS_OK;
 }
 

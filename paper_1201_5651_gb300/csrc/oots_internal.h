@@ -42,6 +42,7 @@ struct TileItem { int job; unsigned short I, J, K, pad; };
 struct DevState {
     double t, t_end;          // current time, end of the advance
     double dt;                // timestep of the substep in flight (0: done)
+    double dt_last;           // the last nonzero timestep (the dt pass's hint)
     double dt_fixed;          // > 0: fixed timestep
     double K1, K3, K4;        // Eq. 4 factors (<= 0: off)
     unsigned long long dt_bits;   // min over cells of the criterion (bits of a positive double)
@@ -59,6 +60,7 @@ struct DevState {
 template <typename Real> struct GridDev {
     int nx, ny, nz;
     long long ncell;
+    long long cell_lo, cell_hi;   // the per-cell passes update cells [cell_lo, cell_hi) of the grid
     Real dx;
     Real sigma0, tau0, alpha;
     const Real *n;            // density (nullptr: uniform n_uniform)
@@ -74,6 +76,8 @@ template <typename Real> struct GridDev {
     int tab[MAX_SRC];         // -1 monochromatic, else table index
     unsigned char pcode[MAX_SRC];  // 0: vertex point source; 1 + 2*axis + back: plane source (qfac = F/dx)
     float lnamp0[MAX_SRC];    // ln(qfac sigma0 dx): a source's largest rate per unit x is qfac sigma0 dx p / r2
+    Real *nstar;              // 3 x MAX_SRC entry columns beyond which a source cannot matter for the
+                              // dt pass (step hint), the half step and the full step (nullptr: none)
     DevState *st;
 };
 

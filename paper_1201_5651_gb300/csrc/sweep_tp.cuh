@@ -8,9 +8,11 @@
 // kernel's early hand-off for a lean tile: T x T x T cells (T = 8), T^2
 // threads, no producer or writer warps, and a shared-memory footprint small
 // enough for about sixteen tiles per SM.  A tile waits for its whole upstream
-// halo, sweeps, then publishes its three downstream faces in the same tagged
-// words as the pipelined kernel (the two kernels share the work list and the
-// face buffers).
+// halo, sweeps, then publishes its three downstream faces as plain values
+// (12 bytes per face cell in the mixed path, half the pipelined kernel's
+// tagged words) followed by one flag per tile, set with release semantics to
+// the launch's epoch; a downstream tile acquires the flags of its upstream
+// tiles before it reads their faces.  The two kernels share the work list.
 //
 // Inside an octant, a cell takes its entry column from the upwind layer of its
 // dominant axis only.  Wherever one axis dominates every cell of a tile (all
@@ -87,24 +89,59 @@ sc_entry_general(const typename ColT<Real>::type *sN, const Real *sW, int h, con
     return ColT<Real>::add(Nref, d);
 }
 
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Reciprocal: correctly rounded in FP64, the fast approximation in the mixed
+// path (a few ulp; the mixed path is judged on its error against FP64).
+__device__ __forceinline__ double tp_rcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ float tp_rcp(float a) { return __fdividef(1.0f, a); }
+
+// Entry column of a cell with one dominant axis: bilinear weights of the
+// entry point on the upwind layer (g1 = c_t1/c_a for the t1-1 neighbour,
+// g2 for t2-1) times the neighbours' factors W (0 outside the octant),
+// normalised; weighted differences to the (0,0) neighbour at h00.
+template <typename Real>
+__device__ __forceinline__ typename ColT<Real>::type
+sc_entry_axis(const typename ColT<Real>::type *sN, const Real *sW, int h00, int s1, int s2, Real g1, Real g2)
+{
+    const Real w00 = (Real(1) - g1) * (Real(1) - g2) * sW[h00];
+    const Real w01 = (Real(1) - g1) * g2 * sW[h00 - s2];
+    const Real w10 = g1 * (Real(1) - g2) * sW[h00 - s1];
+    const Real w11 = g1 * g2 * sW[h00 - s1 - s2];
+    const typename ColT<Real>::type N00 = sN[h00];
+    const Real d = (w01 * ColT<Real>::sub_r(sN[h00 - s2], N00) + w10 * ColT<Real>::sub_r(sN[h00 - s1], N00) +
+                    w11 * ColT<Real>::sub_r(sN[h00 - s1 - s2], N00)) *
+                   tp_rcp(w00 + w01 + w10 + w11);
+    return ColT<Real>::add(N00, d);
+}
+
 template <typename Real, int T>
-__global__ void __launch_bounds__(T *T) sweep_tp_kernel(SweepParams<Real> P)
+__global__ void __launch_bounds__(T *T, sizeof(Real) == 4 ? 16 : 8) sweep_tp_kernel(SweepParams<Real> P)
 {
     typedef typename ColT<Real>::type Col;
     typedef TpLayout<T> L;
     constexpr int NT = L::NT, NC = T * T * T, HSZ = L::HSZ;
     constexpr int SY = L::SY, SZ = L::SZ;
     constexpr int FMAX = T * T;
+    constexpr int NCOMP = tp_face_comps<Real>();
     typedef TileLayout<T, T, T> HL_L;                 // layout the halo and face lists are packed for
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Col *sN = reinterpret_cast<Col *>(smem_raw);      // N_out
     Real *sW = reinterpret_cast<Real *>(sN + HSZ);     // 1/max(dtau, tau0); 0 outside the octant
     Real *sDI = sW + HSZ;                              // increment n x ds, then N_in
-    __shared__ unsigned s_ticket;
+    __shared__ unsigned s_next;                        // the CTA's next ticket (claimed one tile ahead)
+    __shared__ int s_bad;
     const HaloList<T, T, T> &HL = g_halo_list<T, T, T>;
     const FaceList<T, T, T> &FL = g_face_list<T, T, T>;
-    typedef FaceWords<Real> FW;
-    unsigned long long *const faces = P.faces;
     const unsigned epoch = *(volatile unsigned *)P.epoch + 1u;
     const int tid = threadIdx.x;
     const int tu = tid % T, tv = tid / T;              // this thread's cell within a layer or column
@@ -116,17 +153,24 @@ __global__ void __launch_bounds__(T *T) sweep_tp_kernel(SweepParams<Real> P)
         const int lk = (int)(hp / HL_L::SZ) - 1;
         return L::h(li, lj, lk);
     };
+    // a ticket, marked when its grid has already reached its end time
+    auto claim = [&]() {
+        unsigned t = atomicAdd(P.ticket, 1u);
+        if (t < (unsigned)P.nitems && P.grids[P.jobs[P.items[t].job].grid].st->done) t |= 0x80000000u;
+        return t;
+    };
 
+    if (tid == 0) s_next = claim();
+    __syncthreads();
     for (;;) {
-        if (tid == 0) {
-            unsigned t = atomicAdd(P.ticket, 1u);
-            if (t < (unsigned)P.nitems && P.grids[P.jobs[P.items[t].job].grid].st->done) t |= 0x80000000u;
-            s_ticket = t;
-        }
-        __syncthreads();
-        const unsigned tk = s_ticket;
+        const unsigned tk = s_next;
         if ((tk & 0x7fffffffu) >= (unsigned)P.nitems) break;
-        if (tk & 0x80000000u) { __syncthreads(); continue; }
+        if (tk & 0x80000000u) {
+            __syncthreads();
+            if (tid == 0) s_next = claim();
+            __syncthreads();
+            continue;
+        }
         const TileItem it = P.items[tk];
         const Job J = P.jobs[it.job];
         const GridDev<Real> &G = P.grids[J.grid];
@@ -134,8 +178,26 @@ __global__ void __launch_bounds__(T *T) sweep_tp_kernel(SweepParams<Real> P)
         const long long tile_self = J.tile_base + ((long long)it.K * J.nt[1] + it.J) * J.nt[0] + it.I;
         const Real *xin = (P.which == 1) ? G.xh : G.x;
         const Real dx = G.dx, sig = G.sigma0, tau0 = G.tau0;
+        const long long sx = 1, sy = J.nt[0], sz = (long long)J.nt[0] * J.nt[1];
+        const unsigned have = (it.I > 0 ? 1u : 0u) | (it.J > 0 ? 2u : 0u) | (it.K > 0 ? 4u : 0u);
 
-        // 1. own cells: increments n x ds and weight factors (four loads in flight per thread)
+        // 1. the upstream tiles (up to seven: the three face neighbours and the
+        //    four edge and corner ones): wait until each has published in this
+        //    launch (bounded), then the halo is read after the barrier
+        if (tid == 0) s_bad = 0;
+        __syncthreads();
+        if (tid >= 1 && tid <= 7 && (tid & ~have) == 0) {
+            const long long up = tile_self - ((tid & 1) ? sx : 0) - ((tid & 2) ? sy : 0) - ((tid & 4) ? sz : 0);
+            long long spins = 0;
+            unsigned ns = 32;
+            while (ld_acquire_u32(P.tpflags + up) != epoch) {
+                if (++spins > P.spin_limit) { atomicCAS(P.err, 0, (int)DEVERR_TIMEOUT); s_bad = 1; break; }
+                if ((spins & 31) == 0 && *(volatile int *)P.err != 0) { s_bad = 1; break; }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+            }
+        }
+        // 2. own cells: increments n x ds and weight factors (four loads in flight per thread)
         for (int e0 = tid; e0 < NC; e0 += 4 * NT) {
             long long gq[4];
             bool in[4];
@@ -163,48 +225,43 @@ __global__ void __launch_bounds__(T *T) sweep_tp_kernel(SweepParams<Real> P)
                 if (in[u]) {
                     const Real c0 = Real(o0[0] + li) + Real(0.5), c1 = Real(o0[1] + lj) + Real(0.5),
                                c2 = Real(o0[2] + lk) + Real(0.5);
-                    const Real ds = dx * m_sqrt(c0 * c0 + c1 * c1 + c2 * c2) / m_max(c0, m_max(c1, c2));
+                    const Real ds = dx * m_sqrt(c0 * c0 + c1 * c1 + c2 * c2) * tp_rcp(m_max(c0, m_max(c1, c2)));
                     dN = nv[u] * xv[u] * ds;
-                    wf = Real(1) / m_max(sig * dN, tau0);
+                    wf = tp_rcp(m_max(sig * dN, tau0));
                 }
                 sN[h] = ColT<Real>::zero();
                 sW[h] = wf;
                 sDI[h] = dN;
             }
         }
-        // 2. the upstream halo: poll each published cell until its words carry
-        //    this launch's epoch (bounded), or zero it where no upstream tile exists
-        {
-            const long long sx = 1, sy = J.nt[0], sz = (long long)J.nt[0] * J.nt[1];
-            const unsigned have = (it.I > 0 ? 1u : 0u) | (it.J > 0 ? 2u : 0u) | (it.K > 0 ? 4u : 0u);
-            for (int q = tid; q < HL_L::NE; q += NT) {
-                const unsigned en = __ldg(&HL.e[q]);
-                const unsigned mask = en >> 28;
-                const int h = remap(en & 0x3fffu);
-                Col vN = ColT<Real>::zero();
-                Real vW = Real(0);
-                if ((mask & ~have) == 0) {
-                    const long long src = tile_self - ((mask & 1) ? sx : 0) - ((mask & 2) ? sy : 0) - ((mask & 4) ? sz : 0);
-                    const long long o = ((src * 3 + (long long)((en >> 26) & 3u)) * FMAX + ((en >> 14) & 0xfffu)) * FW::W;
-                    bool ok = FW::load(faces + o, epoch, vN, vW);
-                    long long spins = 0;
-                    unsigned ns = 32;
-                    while (!ok) {
-                        if (++spins > P.spin_limit) { atomicCAS(P.err, 0, (int)DEVERR_TIMEOUT); break; }
-                        if ((spins & 31) == 0 && *(volatile int *)P.err != 0) break;
-                        __nanosleep(ns);
-                        if (ns < 256) ns <<= 1;
-                        ok = FW::load(faces + o, epoch, vN, vW);
-                    }
-                    if (!ok) { vN = ColT<Real>::zero(); vW = Real(0); }
+        __syncthreads();
+        // 3. the halo from the upstream tiles' published faces (read past L1)
+        const bool bad = s_bad != 0;
+        for (int q = tid; q < HL_L::NE; q += NT) {
+            const unsigned en = __ldg(&HL.e[q]);
+            const unsigned mask = en >> 28;
+            const int h = remap(en & 0x3fffu);
+            Col vN = ColT<Real>::zero();
+            Real vW = Real(0);
+            if ((mask & ~have) == 0 && !bad) {
+                const long long src = tile_self - ((mask & 1) ? sx : 0) - ((mask & 2) ? sy : 0) - ((mask & 4) ? sz : 0);
+                const Real *f = P.tpfaces + (src * 3 + (long long)((en >> 26) & 3u)) * NCOMP * FMAX + ((en >> 14) & 0xfffu);
+                if (sizeof(Real) == 4) {
+                    vN = ColT<Real>::make(__ldcg(f), __ldcg(f + FMAX));
+                    vW = __ldcg(f + 2 * FMAX);
+                } else {
+                    vN = ColT<Real>::make(__ldcg(f), Real(0));
+                    vW = __ldcg(f + FMAX);
                 }
-                sN[h] = vN;
-                sW[h] = vW;
             }
+            sN[h] = vN;
+            sW[h] = vW;
         }
+        // claim the next tile while this one sweeps
+        if (tid == 0) s_next = claim();
         __syncthreads();
 
-        // 3. one dominant axis over the whole tile (in-octant cells), or mixed
+        // 4. one dominant axis over the whole tile (in-octant cells), or mixed
         const int lo0 = max(o0[0], 0), lo1 = max(o0[1], 0), lo2 = max(o0[2], 0);
         const int hi0 = min(o0[0] + T, J.ext[0]) - 1, hi1 = min(o0[1] + T, J.ext[1]) - 1,
                   hi2 = min(o0[2] + T, J.ext[2]) - 1;
@@ -234,43 +291,51 @@ __global__ void __launch_bounds__(T *T) sweep_tp_kernel(SweepParams<Real> P)
                 const int ia = oa + l;
                 if (col_in && ia >= 0 && ia < exta) {
                     const int h = h0 + l * sa;
-                    const int h00 = h - sa;
-                    const Real ica = Real(1) / Real(2 * ia + 1);
-                    const Real g1 = c1 * ica, g2 = c2 * ica;            // weights of the t1-1 and t2-1 neighbours
-                    const Real w00 = (Real(1) - g1) * (Real(1) - g2) * sW[h00];
-                    const Real w01 = (Real(1) - g1) * g2 * sW[h00 - s2];
-                    const Real w10 = g1 * (Real(1) - g2) * sW[h00 - s1];
-                    const Real w11 = g1 * g2 * sW[h00 - s1 - s2];
-                    const Col N00 = sN[h00];
-                    const Real d = (w01 * ColT<Real>::sub_r(sN[h00 - s2], N00) + w10 * ColT<Real>::sub_r(sN[h00 - s1], N00) +
-                                    w11 * ColT<Real>::sub_r(sN[h00 - s1 - s2], N00)) /
-                                   (w00 + w01 + w10 + w11);
-                    const Col Nin = ColT<Real>::add(N00, d);
+                    const Real ica = tp_rcp(Real(2 * ia + 1));
+                    const Col Nin = sc_entry_axis<Real>(sN, sW, h - sa, s1, s2, c1 * ica, c2 * ica);
                     sN[h] = ColT<Real>::add(Nin, sDI[h]);
                     sDI[h] = ColT<Real>::to_real(Nin);
                 }
                 __syncthreads();
             }
         } else {
-            // plane by plane (li + lj + lk = m), one thread per (lj, lk) column
+            // plane by plane (li + lj + lk = m), one thread per (lj, lk) column;
+            // cells with one dominant axis take the cheap form, tied cells the
+            // average over their tied axes, the vertex cell N_in = 0
             const int lj = tu, lk = tv;
+            const int j = o0[1] + lj, k = o0[2] + lk;
+            const bool col_in = j >= 0 && k >= 0 && j < J.ext[1] && k < J.ext[2];
+            const int m_lo = lj + lk, m_hi = lj + lk + T - 1;
             for (int m = 0; m < L::NP; m++) {
                 const int li = m - lj - lk;
-                if (li >= 0 && li < T) {
-                    const int idx[3] = {o0[0] + li, o0[1] + lj, o0[2] + lk};
-                    if (idx[0] >= 0 && idx[1] >= 0 && idx[2] >= 0 && idx[0] < J.ext[0] && idx[1] < J.ext[1] &&
-                        idx[2] < J.ext[2]) {
-                        const int h = L::h(li, lj, lk);
-                        const Col Nin = sc_entry_general<Real, T>(sN, sW, h, idx);
-                        sN[h] = ColT<Real>::add(Nin, sDI[h]);
-                        sDI[h] = ColT<Real>::to_real(Nin);
+                const int i = o0[0] + li;
+                if (col_in && m >= m_lo && m <= m_hi && i >= 0 && i < J.ext[0]) {
+                    const int h = L::h(li, lj, lk);
+                    const int c2i = 2 * i + 1, c2j = 2 * j + 1, c2k = 2 * k + 1;
+                    const int cm = max(c2i, max(c2j, c2k));
+                    const int ntied = (c2i == cm) + (c2j == cm) + (c2k == cm);
+                    Col Nin;
+                    if (ntied == 1) {
+                        const int a = c2i == cm ? 0 : (c2j == cm ? 1 : 2);
+                        const int sa = a == 0 ? 1 : (a == 1 ? SY : SZ);
+                        const int s1 = a == 0 ? SY : (a == 1 ? SZ : 1);
+                        const int s2 = a == 0 ? SZ : (a == 1 ? 1 : SY);
+                        const int ct1 = a == 0 ? c2j : (a == 1 ? c2k : c2i);
+                        const int ct2 = a == 0 ? c2k : (a == 1 ? c2i : c2j);
+                        const Real ica = tp_rcp(Real(cm));
+                        Nin = sc_entry_axis<Real>(sN, sW, h - sa, s1, s2, Real(ct1) * ica, Real(ct2) * ica);
+                    } else {
+                        const int idx[3] = {i, j, k};
+                        Nin = sc_entry_general<Real, T>(sN, sW, h, idx);
                     }
+                    sN[h] = ColT<Real>::add(Nin, sDI[h]);
+                    sDI[h] = ColT<Real>::to_real(Nin);
                 }
                 __syncthreads();
             }
         }
 
-        // 4. entry columns of the tile's cells, then its downstream faces
+        // 5. entry columns of the tile's cells, then its downstream faces and flag
         Real *Nout = (P.which == 1 ? G.N2 : G.N1) + (long long)J.src * G.ncell;
         for (int e = tid; e < NC; e += NT) {
             const int li = e % T, lj = (e / T) % T, lk = e / (T * T);
@@ -283,11 +348,25 @@ __global__ void __launch_bounds__(T *T) sweep_tp_kernel(SweepParams<Real> P)
             }
         }
         if (tile_self != P.skip_publish) {
-            unsigned long long *const fbase = faces + tile_self * 3 * FMAX * FW::W;
+            Real *fbase = P.tpfaces + tile_self * 3 * NCOMP * FMAX;
             for (int q = tid; q < FaceList<T, T, T>::N; q += NT) {
                 const unsigned en = __ldg(&FL.e[q]);
                 const int h = remap(en & 0x3fffu);
-                FW::store(fbase + (((en >> 26) & 3u) * FMAX + ((en >> 14) & 0xfffu)) * FW::W, sN[h], sW[h], epoch);
+                Real *f = fbase + ((en >> 26) & 3u) * NCOMP * FMAX + ((en >> 14) & 0xfffu);
+                const Col v = sN[h];
+                if (sizeof(Real) == 4) {
+                    __stcg(f, ColT<Real>::hi(v));
+                    __stcg(f + FMAX, ColT<Real>::lo(v));
+                    __stcg(f + 2 * FMAX, sW[h]);
+                } else {
+                    __stcg(f, ColT<Real>::hi(v));
+                    __stcg(f + FMAX, sW[h]);
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();
+                st_release_u32(P.tpflags + tile_self, epoch);
             }
         }
         __syncthreads();

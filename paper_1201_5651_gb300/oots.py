@@ -39,7 +39,9 @@ EXPORTS = [
     "oots_batch_create", "oots_batch_advance", "oots_batch_destroy", "oots_set_tile_shape",
     "oots_tile_shape_info", "oots_debug_set", "oots_version", "oots_run_substeps", "oots_profile_substep",
     "oots_trace_noalloc", "oots_add_plane_source", "oots_batch_run_substeps",
+    "oots_set_partition", "oots_run_phase", "oots_array_device",
 ]
+OOTS_PH_TRACE1, OOTS_PH_DT, OOTS_PH_STEP1, OOTS_PH_TRACE2, OOTS_PH_FULL = 0, 1, 2, 3, 4
 KERNEL_KINDS = {1: "sweep1", 2: "ratedt", 3: "final0", 4: "half", 5: "sweep2", 6: "full", 7: "final1", 8: "implicit",
                 9: "half_general", 10: "full_general", 11: "plane_trace", 12: "plane_implicit"}
 
@@ -112,6 +114,9 @@ def load(build_if_missing: bool = True):
         "oots_batch_advance": ([vp, P(dp), P(ctypes.c_longlong)], ip),
         "oots_batch_destroy": ([vp], ip),
         "oots_batch_run_substeps": ([vp, ctypes.c_longlong, P(dp)], ip),
+        "oots_set_partition": ([vp, ctypes.c_ulonglong, ip, ip], ip),
+        "oots_run_phase": ([vp, ip, P(dp)], ip),
+        "oots_array_device": ([vp, ip, ip, P(vp), P(ctypes.c_ulonglong)], ip),
         "oots_set_tile_shape": ([vp, ip], ip),
         "oots_tile_shape_info": ([ip, P(ip)], ip),
         "oots_debug_set": ([vp, ip, ctypes.c_longlong], ip),
@@ -326,6 +331,22 @@ class Context:
 
     def set_time(self, t: float):
         return self._c(self.lib.oots_set_time(self.h, float(t)))
+
+    # partitioned runs (one process per GPU)
+    def set_partition(self, src_mask: int = (1 << 64) - 1, z0: int = 0, z1: int = 0):
+        return self._c(self.lib.oots_set_partition(self.h, ctypes.c_ulonglong(src_mask), int(z0), int(z1)))
+
+    def run_phase(self, phase: int, value: float = 0.0) -> float:
+        v = ctypes.c_double(value)
+        self._c(self.lib.oots_run_phase(self.h, int(phase), ctypes.byref(v)))
+        return v.value
+
+    def array_device(self, kind: int, source: int = 0):
+        """(device address, bytes) of x (0), x_half (1), first (2) or second (3) columns of a source."""
+        p = ctypes.c_void_p()
+        n = ctypes.c_ulonglong()
+        self._c(self.lib.oots_array_device(self.h, int(kind), int(source), ctypes.byref(p), ctypes.byref(n)))
+        return p.value, n.value
 
     # caller-owned device memory (e.g. torch tensors' data_ptr())
     def set_neutral_fraction_device(self, ptr: int, float32: bool):

@@ -7,6 +7,7 @@ a capture sees exactly the launches of that substep.  Prints the per-launch
 durations that the library's own events measured for the same substep.
 
     python -m paper_1201_5651_gb300.profile_substep --workload lognormal128_bb --precision mixed --shape 2
+    python -m paper_1201_5651_gb300.profile_substep --workload multisource512_bb --shape 7 --t0 0.005 --substeps 3
 """
 from __future__ import annotations
 
@@ -15,6 +16,10 @@ import argparse
 from . import inputs, oots
 
 WORKLOADS = {
+    # 16 blackbody sources in lognormal gas (the many-source workload at full size and at 1/8 of its cells)
+    "multisource512_bb": lambda: inputs.multisource(512),
+    "multisource256_bb": lambda: inputs.multisource(256),
+    "clumpy256_mono": lambda: inputs.clumpy(256, 1.5, 1203, 1303, 200, Q=1e48, box_rs=2.5, spectrum="mono"),
     "lognormal128_bb": lambda: inputs.lognormal_bb(128, 1.0, 1202, Q=1e48, T=4e4, box_rs=2.5),
     "lognormal64_bb": lambda: inputs.lognormal_bb(64, 1.0, 1202, Q=1e48, T=4e4, box_rs=2.5),
     "stromgren32": lambda: inputs.stromgren_corner(32),
@@ -32,6 +37,7 @@ def main(argv=None):
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--shape", type=int, default=-1, help="tile shape id (-1: library default)")
     ap.add_argument("--t0", type=float, default=0.05, help="start time in units of t_rec (0: start at once)")
+    ap.add_argument("--substeps", type=int, default=1, help="substeps inside the profiler range")
     args = ap.parse_args(argv)
 
     import torch
@@ -44,11 +50,12 @@ def main(argv=None):
     c.profile_substep()                       # build and warm up every launch
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStart()
-    prof = c.profile_substep()
+    profs = [c.profile_substep() for _ in range(args.substeps)]
     torch.cuda.synchronize()
     torch.cuda.cudart().cudaProfilerStop()
-    for k, ms in prof:
-        print(f"{k:14s} {ms * 1e3:10.1f} us")
+    for i, prof in enumerate(profs):
+        for k, ms in prof:
+            print(f"{i:3d} {k:14s} {ms * 1e3:10.1f} us")
 
 
 if __name__ == "__main__":

@@ -63,6 +63,9 @@ def test_null_arguments_are_rejected():
     assert lib.oots_destroy(None) == oots.OOTS_OK
     assert lib.oots_batch_create(None, None, 0) == oots.OOTS_E_INVAL
     assert lib.oots_batch_run_substeps(None, 1, None) == oots.OOTS_E_INVAL
+    assert lib.oots_set_partition(None, 1, 0, 0) == oots.OOTS_E_INVAL
+    assert lib.oots_run_phase(None, 0, None) == oots.OOTS_E_INVAL
+    assert lib.oots_array_device(None, 0, 0, None, None) == oots.OOTS_E_INVAL
     h = ctypes.c_void_p()
     assert lib.oots_create(ctypes.byref(h), 0, 7) == oots.OOTS_E_INVAL
     assert lib.oots_add_plane_source(None, 0, 1, 1e9, oots.OOTS_MONO, 0.0, None) == oots.OOTS_E_INVAL
