@@ -260,7 +260,7 @@ def _describe_tile(shape):
     if shape is None:
         return None
     dims = oots.oots_tile_shape_info(shape)[1]
-    return {"id": shape, "dims": list(dims), "kernel": "throughput" if shape == 7 else "pipelined"}
+    return {"id": shape, "dims": list(dims), "kernel": "throughput" if shape in (7, 8) else "pipelined"}
 
 
 def _roofline(prof_avg, ms_per_step, ncell, nsrc, n_array, workload, tile_shape):

@@ -311,7 +311,11 @@ int oots_tile_shape_info(int shape, int dims[3]);
  * progress (-1 = none), which makes its downstream waits run out and the call
  * return OOTS_E_DEVICE_TIMEOUT without faulting the device; key 3 = planes a
  * sweep tile completes between two progress publications (1..64; 0 = the
- * default of 4).  OOTS_E_INVAL for an unknown key or a value out of range. */
+ * default of 4); key 4 = where the sweep's tiles start: 0 (default) at
+ * multiples of the tile size in global coordinates (rows of x aligned to
+ * memory), 1 at the octant's origin (the octant's diagonal planes then cut
+ * only the tiles on the tile diagonals).  OOTS_E_INVAL for an unknown key or
+ * a value out of range. */
 int oots_debug_set(oots_ctx *ctx, int key, long long value);
 
 /* ---- allocation-free trace --------------------------------------------------------------- */

@@ -16,6 +16,8 @@ Runs go through the public C ABI on the mixed path.
 
     python -m paper_1201_5651_gb300.accuracy_study --dtau 1 3 10 30 --schemes 1 3 --criteria 0 1 2 3 4 \
         --out study.json
+    python -m paper_1201_5651_gb300.accuracy_study --density 100 1000 --dtau 3 10 30 --schemes 1 2 3 \
+        --criteria 0 1 2 3 4 5 6 7 8 9 10 11 12 --budget 20 --out map.json
 """
 from __future__ import annotations
 
@@ -64,8 +66,8 @@ def run(w, scheme: int, crit: int, precision: str = "mixed", budget_s: float = 1
     return out, x
 
 
-def study(dtau0: float, schemes, criteria, tau_s: float, precision: str, budget_s: float):
-    w = inputs.stromgren_bb(dtau0, tau_s=tau_s)
+def study(dtau0: float, schemes, criteria, tau_s: float, precision: str, budget_s: float, n_H: float = 10.0):
+    w = inputs.stromgren_bb(dtau0, tau_s=tau_s, n_H=n_H)
     ref, xref = run(w, 3, 12, precision, budget_s=10 * budget_s)
     rows = []
     for s in schemes:
@@ -78,7 +80,22 @@ def study(dtau0: float, schemes, criteria, tau_s: float, precision: str, budget_
                 r["front_err"] = [a / b - 1.0 for a, b in zip(r["reff"], ref["reff"])]
                 r["l1"] = float(np.abs(x - xref).mean())
             rows.append(r)
-    return {"dtau0": dtau0, "n": w.nx, "tau_s": tau_s, "t_rec": w.t_rec, "reference": ref, "runs": rows}
+    return {"dtau0": dtau0, "n_H": n_H, "n": w.nx, "tau_s": tau_s, "t_rec": w.t_rec, "reference": ref, "runs": rows}
+
+
+def cheapest(res, scheme: int, l1_max: float, cost: str = "seconds"):
+    """The cheapest complete run of `scheme` whose L1 error (Eq. 6) is at most
+    l1_max: (cost, criterion), or None.  cost "traces" counts the traces a run
+    did (A3 two per substep, A2 and A1 one), a cost that does not depend on the
+    machine's load."""
+    best = None
+    for q in res["runs"]:
+        if q["scheme"] != scheme or "l1" not in q or q["l1"] > l1_max:
+            continue
+        v = q["seconds"] if cost == "seconds" else q["nsub"] * (2 if scheme == 3 else 1)
+        if best is None or v < best[0]:
+            best = (v, q["crit"])
+    return best
 
 
 def main(argv=None):
@@ -87,21 +104,23 @@ def main(argv=None):
     ap.add_argument("--schemes", type=int, nargs="+", default=[1, 3])
     ap.add_argument("--criteria", type=int, nargs="+", default=[0, 1, 2, 3, 4])
     ap.add_argument("--tau-s", type=float, default=240.0)
+    ap.add_argument("--density", type=float, nargs="+", default=[10.0], help="hydrogen densities n_H [cm^-3]")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--budget", type=float, default=60.0, help="wall seconds per run before it is cut short")
     ap.add_argument("--out", default=None)
     args = ap.parse_args(argv)
     res = []
-    for d in args.dtau:
-        r = study(d, args.schemes, args.criteria, args.tau_s, args.precision, args.budget)
-        res.append(r)
-        print(f"dtau0 {d:g}: {r['n']}^3 cells, reference A3-dt12 {r['reference']['nsub']} substeps "
-              f"{r['reference']['seconds']:.1f} s", flush=True)
-        for q in r["runs"]:
-            fe = " ".join(f"{v:+.4f}" for v in q.get("front_err", [])) or "incomplete"
-            l1 = f"{q['l1']:.2e}" if "l1" in q else "-"
-            print(f"  A{q['scheme']}-dt{q['crit']:02d}  front err at {TIMES} t_rec: {fe}  L1 {l1}  "
-                  f"{q['nsub']} substeps {q['seconds']:.2f} s", flush=True)
+    for nh in args.density:
+        for d in args.dtau:
+            r = study(d, args.schemes, args.criteria, args.tau_s, args.precision, args.budget, n_H=nh)
+            res.append(r)
+            print(f"n_H {nh:g}, dtau0 {d:g}: {r['n']}^3 cells, reference A3-dt12 {r['reference']['nsub']} substeps "
+                  f"{r['reference']['seconds']:.1f} s", flush=True)
+            for q in r["runs"]:
+                fe = " ".join(f"{v:+.4f}" for v in q.get("front_err", [])) or "incomplete"
+                l1 = f"{q['l1']:.2e}" if "l1" in q else "-"
+                print(f"  A{q['scheme']}-dt{q['crit']:02d}  front err at {TIMES} t_rec: {fe}  L1 {l1}  "
+                      f"{q['nsub']} substeps {q['seconds']:.2f} s", flush=True)
     if args.out:
         with open(args.out, "w") as f:
             json.dump(res, f, indent=1)

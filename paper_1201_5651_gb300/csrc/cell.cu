@@ -424,25 +424,41 @@ __device__ Real negligible_column(const GridDev<Real> &G, const DevTable<Real> *
 // Returns how many there are; NK + 1 when there are more than NK.
 // nstar (may be null): per source a column beyond which the source is left
 // out without forming its bound.
+// The entry columns of sources s0 .. s0+7 at cell g, loaded together (eight
+// loads in flight instead of one latency per source).
+template <typename Real>
+__device__ __forceinline__ void load_columns8(const GridDev<Real> &G, const Real *Ncol, int s0, long long g, Real *Nb)
+{
+#pragma unroll
+    for (int q = 0; q < 8; q++) Nb[q] = s0 + q < G.nsrc ? Ncol[(long long)(s0 + q) * G.ncell + g] : Real(0);
+}
+
 template <typename Real, int NK>
 __device__ __forceinline__ int gather_rates(const GridDev<Real> &G, const Real *Ncol, const DevTable<Real> *tabs,
                                             int X, int Y, int Z, long long g, Real n, float lnthr, SrcRate<Real> *r,
                                             const Real *nstar)
 {
     int cnt = 0;
-    for (int s = 0; s < G.nsrc; s++) {
-        const Real N = Ncol[(long long)s * G.ncell + g];
-        if (nstar && N >= nstar[s]) continue;
-        int i, j, k;
-        const float r2 = src_cell(G, s, X, Y, Z, i, j, k);
-        if (!(src_lnamp(G, tabs, s, r2, N) > lnthr)) continue;
-        if (cnt == NK) return NK + 1;
-        SrcRate<Real> t;
-        src_rate<Real>(t, G.qfac[s], G.tab[s], G.sigma0, G.dx, n, G.pcode[s] != 0, i, j, k, N, tabs);
+    for (int s0 = 0; s0 < G.nsrc; s0 += 8) {
+        Real Nb[8];
+        load_columns8(G, Ncol, s0, g, Nb);
 #pragma unroll
-        for (int q = 0; q < NK; q++)
-            if (q == cnt) r[q] = t;
-        cnt++;
+        for (int q = 0; q < 8; q++) {
+            const int s = s0 + q;
+            if (s >= G.nsrc) break;
+            const Real N = Nb[q];
+            if (nstar && N >= nstar[s]) continue;
+            int i, j, k;
+            const float r2 = src_cell(G, s, X, Y, Z, i, j, k);
+            if (!(src_lnamp(G, tabs, s, r2, N) > lnthr)) continue;
+            if (cnt == NK) return NK + 1;
+            SrcRate<Real> t;
+            src_rate<Real>(t, G.qfac[s], G.tab[s], G.sigma0, G.dx, n, G.pcode[s] != 0, i, j, k, N, tabs);
+#pragma unroll
+            for (int u = 0; u < NK; u++)
+                if (u == cnt) r[u] = t;
+            cnt++;
+        }
     }
     return cnt;
 }
@@ -593,29 +609,26 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_ker
             const Real c = G.alpha * n;
             const float lnthr = s_lnthr;
             if (OP == OP_RATEDT) {
-                // Eq. 4 with T fixed: K1 t_rec, K3 max(0.05, x)/|dx/dt|, K4/|dx/dt|.
-                // The sources that can matter within the hint, by their bounds; a
-                // cell that none of them lights within the hint is photon-free
-                // (F = F' = 0) and only recombines.
+                // Eq. 4 with T fixed: K1 t_rec, K3 max(0.05, x)/|dx/dt|, K4/|dx/dt|,
+                // from the sources that can matter within the hint (their bounds);
+                // a cell that none of them reaches is photon-free (F = F' = 0).
                 const Real *nst = (G.nstar && !verify) ? G.nstar : nullptr;
                 float ampsum = 0.0f;
-                for (int s = 0; s < G.nsrc; s++) {
-                    const Real N = G.N1[(long long)s * G.ncell + g];
-                    if (nst && N >= nst[s]) continue;
-                    int i, j, k;
-                    const float r2 = src_cell(G, s, X, Y, Z, i, j, k);
-                    const float la = src_lnamp(G, tabs, s, r2, N);
-                    if (la > lnthr) ampsum += __expf(la);
-                }
-                const bool exact = !(s_hint < 1e300) || double(ampsum) * s_hint > 1e-3 * double(RealLimits<Real>::eps());
                 Real F = Real(0), dF = Real(0);
-                if (exact) {
-                    for (int s = 0; s < G.nsrc; s++) {
-                        const Real N = G.N1[(long long)s * G.ncell + g];
+                for (int s0 = 0; s0 < G.nsrc; s0 += 8) {
+                    Real Nb[8];
+                    load_columns8(G, G.N1, s0, g, Nb);
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const int s = s0 + q;
+                        if (s >= G.nsrc) break;
+                        const Real N = Nb[q];
                         if (nst && N >= nst[s]) continue;
                         int i, j, k;
                         const float r2 = src_cell(G, s, X, Y, Z, i, j, k);
-                        if (!(src_lnamp(G, tabs, s, r2, N) > lnthr)) continue;
+                        const float la = src_lnamp(G, tabs, s, r2, N);
+                        if (!(la > lnthr)) continue;
+                        ampsum += __expf(la);
                         SrcRate<Real> t;
                         src_rate<Real>(t, G.qfac[s], G.tab[s], G.sigma0, G.dx, n, G.pcode[s] != 0, i, j, k, N, tabs);
                         CellODE<Real> C1;

@@ -20,11 +20,15 @@ template <typename Real> struct ColT;
     X(4, 8, 8, 8)      \
     X(5, 16, 16, 8)    \
     X(6, 8, 8, 4)
-// Shape 7 tiles the octants like shape 4 (8 x 8 x 8) but traces them with the
-// throughput kernel (whole tiles, 64 threads, layer sweeps off the diagonal
-// planes; sweep_tp.cuh); the implicit sweep (A1) runs shape 4's kernel on it.
-enum { NUM_SHAPES = 8, SHAPE_TP8 = 7 };
-static const int SHAPE_DIMS[NUM_SHAPES][3] = {{16, 8, 8}, {16, 8, 4}, {16, 16, 16}, {32, 8, 4}, {8, 8, 8}, {16, 16, 8}, {8, 8, 4}, {8, 8, 8}};
+// Shapes 7 and 8 tile the octants like shapes 4 (8 x 8 x 8) and 0 (16 x 8 x 8)
+// but trace them with the throughput kernel (whole tiles, 64 threads, layer
+// sweeps off the diagonal planes; sweep_tp.cuh); the implicit sweep (A1) runs
+// the pipelined kernel of the same tile (shape 4 or 0) on them.
+enum { NUM_SHAPES = 9, SHAPE_TP8 = 7, SHAPE_TP16 = 8 };
+static const int SHAPE_DIMS[NUM_SHAPES][3] = {{16, 8, 8}, {16, 8, 4}, {16, 16, 16}, {32, 8, 4}, {8, 8, 8},
+                                              {16, 16, 8}, {8, 8, 4}, {8, 8, 8}, {16, 8, 8}};
+inline bool is_tp_shape(int shape) { return shape == SHAPE_TP8 || shape == SHAPE_TP16; }
+inline int tp_twin(int shape) { return shape == SHAPE_TP8 ? 4 : 0; }   // pipelined kernel on the same tiles
 
 template <typename Real> struct SweepParams {
     const GridDev<Real> *grids;

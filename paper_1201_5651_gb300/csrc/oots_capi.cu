@@ -111,6 +111,7 @@ struct oots_ctx {
     long long spin_limit = 1ll << 22;
     long long skip_publish = -1;
     int sweep_chunk = 0;               // planes per progress step of the sweep (0: default)
+    int tile_align = 0;                // tile origins: 0 global multiples of the tile (x rows aligned), 1 the octant's
     size_t rsize = 8;
     void *d_x = nullptr, *d_n = nullptr, *d_xh = nullptr, *d_N1 = nullptr, *d_N2 = nullptr;
     void *d_stage = nullptr;           // ncell doubles: host arrays pass through it (allocated on first use)
@@ -314,7 +315,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
                         J.ext[a] = J.sg[a] > 0 ? n3[a] - S.v[a] : S.v[a];
                         if (J.ext[a] <= 0) empty = true;
                         const int r = S.v[a] % T3[a];
-                        J.off[a] = J.sg[a] > 0 ? r : (T3[a] - r) % T3[a];
+                        J.off[a] = c->tile_align ? 0 : (J.sg[a] > 0 ? r : (T3[a] - r) % T3[a]);
                         J.nt[a] = (J.ext[a] + J.off[a] + T3[a] - 1) / T3[a];
                     }
                     if (empty) continue;
@@ -375,12 +376,12 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
             // The pipelined kernel publishes tagged words; the throughput kernel
             // (shape 7) plain values and a flag per tile; A1 runs the pipelined
             // kernel on shape 7's tiles.
-            if (shape != SHAPE_TP8 || scheme == OOTS_A1) {
+            if (!is_tp_shape(shape) || scheme == OOTS_A1) {
                 const size_t fbytes = (size_t)ntiles * 3 * FMAX * face_words<Real>() * sizeof(unsigned long long);
                 CU(cudaMalloc(&d_faces, fbytes));
                 CU(cudaMemset(d_faces, 0, fbytes));
             }
-            if (shape == SHAPE_TP8) {
+            if (is_tp_shape(shape)) {
                 CU(cudaMalloc(&d_tpfaces, (size_t)ntiles * 3 * FMAX * tp_face_comps<Real>() * sizeof(Real)));
                 CU(cudaMalloc(&d_tpflags, (size_t)ntiles * sizeof(unsigned)));
                 CU(cudaMemset(d_tpflags, 0, (size_t)ntiles * sizeof(unsigned)));
@@ -1259,6 +1260,9 @@ int oots_debug_set(oots_ctx *c, int key, long long value)
     } else if (key == 3) {
         if (value < 0 || value > 64) return fail(OOTS_E_INVAL, "sweep chunk %lld", value);
         c->sweep_chunk = (int)value;
+    } else if (key == 4) {
+        if (value != 0 && value != 1) return fail(OOTS_E_INVAL, "tile alignment %lld", value);
+        c->tile_align = (int)value;
     } else {
         return fail(OOTS_E_INVAL, "debug key %d", key);
     }

@@ -787,6 +787,7 @@ template <typename Real>
 bool sweep_shape_ok(int shape)
 {
     if (shape == SHAPE_TP8) return (int)sweep_tp_smem<Real, 8>() <= max_optin_smem() && sweep_shape_ok<Real>(4);
+    if (shape == SHAPE_TP16) return (int)sweep_tp_smem<Real, 16>() <= max_optin_smem() && sweep_shape_ok<Real>(0);
     size_t sm = 0;
 #define OOTS_SM(ID, TX, TY, TZ) if (shape == ID) sm = sweep_smem<Real, TX, TY, TZ>();
     OOTS_SHAPES(OOTS_SM)
@@ -799,9 +800,12 @@ int sweep_occupancy(int shape, int mode)
 {
     int nb = 0;
     cudaError_t e = cudaSuccess;
-    if (shape == SHAPE_TP8) {
-        if (mode == 1) return sweep_occupancy<Real>(4, 1);
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_tp_kernel<Real, 8>, 64, sweep_tp_smem<Real, 8>());
+    if (is_tp_shape(shape)) {
+        if (mode == 1) return sweep_occupancy<Real>(tp_twin(shape), 1);
+        if (shape == SHAPE_TP8)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_tp_kernel<Real, 8>, 64, sweep_tp_smem<Real, 8>());
+        else
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, sweep_tp_kernel<Real, 16>, 64, sweep_tp_smem<Real, 16>());
         return (e == cudaSuccess && nb > 0) ? nb : 1;
     }
 #define OOTS_OCC(ID, TX, TY, TZ)                                                                      \
@@ -823,9 +827,10 @@ cudaError_t launch_sweep(const SweepParams<Real> &P, int shape, int mode, int nb
     long long nb = nblocks;
     if (nb > P.nitems) nb = P.nitems;
     if (nb < 1) nb = 1;
-    if (shape == SHAPE_TP8) {
-        if (mode == 1) return launch_sweep<Real>(P, 4, 1, nblocks, s);
-        sweep_tp_kernel<Real, 8><<<(int)nb, 64, sweep_tp_smem<Real, 8>(), s>>>(P);
+    if (is_tp_shape(shape)) {
+        if (mode == 1) return launch_sweep<Real>(P, tp_twin(shape), 1, nblocks, s);
+        if (shape == SHAPE_TP8) sweep_tp_kernel<Real, 8><<<(int)nb, 64, sweep_tp_smem<Real, 8>(), s>>>(P);
+        else sweep_tp_kernel<Real, 16><<<(int)nb, 64, sweep_tp_smem<Real, 16>(), s>>>(P);
         return cudaGetLastError();
     }
 #define OOTS_LAUNCH(ID, TX, TY, TZ)                                                         \
@@ -850,6 +855,11 @@ cudaError_t prepare_sweeps()
     if ((int)sweep_tp_smem<Real, 8>() <= max_optin_smem()) {
         e2 = cudaFuncSetAttribute(sweep_tp_kernel<Real, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)sweep_tp_smem<Real, 8>());
+        if (e2 != cudaSuccess) e = e2;
+    }
+    if ((int)sweep_tp_smem<Real, 16>() <= max_optin_smem()) {
+        e2 = cudaFuncSetAttribute(sweep_tp_kernel<Real, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sweep_tp_smem<Real, 16>());
         if (e2 != cudaSuccess) e = e2;
     }
     return e;

@@ -3,24 +3,25 @@
 // Sect. 5: octants traced outward from the source vertex independently).
 //
 // When many sources or grids share a launch, tiles are plentiful and the
-// wavefront's depth no longer sets the pace: the per-cell instruction count
-// and the warps each SM keeps busy do.  This kernel trades the pipelined
-// kernel's early hand-off for a lean tile: T x T x T cells (T = 8), T^2
-// threads, no producer or writer warps, and a shared-memory footprint small
-// enough for about sixteen tiles per SM.  A tile waits for its whole upstream
-// halo, sweeps, then publishes its three downstream faces as plain values
-// (12 bytes per face cell in the mixed path, half the pipelined kernel's
-// tagged words) followed by one flag per tile, set with release semantics to
-// the launch's epoch; a downstream tile acquires the flags of its upstream
-// tiles before it reads their faces.  The two kernels share the work list.
+// wavefront's depth no longer sets the pace: the per-cell instruction count,
+// the memory latency each tile waits through and the tiles each SM keeps in
+// flight do.  This kernel trades the pipelined kernel's early hand-off for a
+// lean tile: TX x 8 x 8 cells (TX = 8 or 16), 64 threads, no producer or
+// writer warps, and a shared-memory footprint small enough for 9-16 tiles per
+// SM.  A tile waits for its whole upstream halo, sweeps, then publishes its
+// three downstream faces as plain values (12 bytes per face cell in the mixed
+// path, half the pipelined kernel's tagged words) followed by one flag per
+// tile, set with release semantics to the launch's epoch; a downstream tile
+// acquires the flags of its upstream tiles before it reads their faces.  The
+// two kernels share the work list.
 //
 // Inside an octant, a cell takes its entry column from the upwind layer of its
 // dominant axis only.  Wherever one axis dominates every cell of a tile (all
 // tiles off the octant's diagonal planes i = j, j = k, i = k), the tile is
-// therefore swept layer by layer along that axis, with one thread per cell of
-// the layer: T steps, every thread busy at each.  The other tiles hold tied
-// cells, which average the interpolations along their tied axes; they are
-// swept plane by plane (i + j + k) with one thread per (j,k) column.
+// therefore swept layer by layer along that axis, every thread busy at each
+// step (one or two cells of the layer).  The other tiles hold tied cells,
+// which average the interpolations along their tied axes; they are swept
+// plane by plane (i + j + k) with one thread per (j,k) column.
 //
 // Included by sweep_impl.cuh ahead of the launch wrappers.
 #pragma once
@@ -28,23 +29,49 @@
 namespace oots {
 
 // Shared-memory layout of a throughput tile with its one-cell upstream halo:
-// index (lk+1) SZ + (lj+1) SY + (li+1).  The strides keep a layer's accesses
-// (lanes over two of the three axes) free of bank conflicts for two of the
-// three layer orientations and at most two-way for the third.
-template <int T> struct TpLayout {
-    static constexpr int SY = T + 1;
-    static constexpr int SZ = T == 8 ? 88 : (T + 1) * (T + 1);
-    static constexpr int HSZ = (T + 1) * SZ;
-    static constexpr int NT = T * T;
-    static constexpr int NP = 3 * T - 2;
+// index (lk+1) SZ + (lj+1) SY + (li+1).  The strides were chosen by counting
+// bank conflicts over the access patterns of the passes (cell loads, the
+// three layer orientations, the diagonal planes): at most two-way.
+template <int TX> struct TpLayout {
+    static constexpr int TY = 8, TZ = 8;
+    static constexpr int SY = TX == 8 ? 9 : 18;
+    static constexpr int SZ = TX == 8 ? 88 : 169;
+    static constexpr int HSZ = (TZ + 1) * SZ;
+    static constexpr int NT = TY * TZ;                 // threads
+    static constexpr int NC = TX * TY * TZ;            // cells
+    static constexpr int NP = TX + TY + TZ - 2;        // planes i + j + k of a tile
     static constexpr OOTS_HD int h(int li, int lj, int lk) { return (lk + 1) * SZ + (lj + 1) * SY + (li + 1); }
-    static_assert(T * SY + T < SZ, "rows fit below the next plane");
+    static_assert(TY * SY + TX < SZ, "rows fit below the next plane");
     static_assert(HSZ < (1 << 14), "halo entry packing");
 };
 
-template <typename Real, int T> constexpr size_t sweep_tp_smem()
+// The halo and face lists of a tile (built for the pipelined layout),
+// repacked with the throughput layout's shared-memory index in the low 14 bits.
+template <int TX> struct TpLists {
+    unsigned halo[TileLayout<TX, 8, 8>::NE];
+    unsigned face[FaceList<TX, 8, 8>::N];
+};
+template <int TX> constexpr unsigned tp_repack(unsigned e)
 {
-    return (size_t)TpLayout<T>::HSZ * (sizeof(typename ColT<Real>::type) + 2 * sizeof(Real));
+    typedef TileLayout<TX, 8, 8> P;
+    const int hp = (int)(e & 0x3fffu);
+    const int li = hp % P::SZ % P::SY - 1, lj = hp % P::SZ / P::SY - 1, lk = hp / P::SZ - 1;
+    return (e & ~0x3fffu) | (unsigned)TpLayout<TX>::h(li, lj, lk);
+}
+template <int TX> constexpr TpLists<TX> make_tp_lists()
+{
+    TpLists<TX> R{};
+    const HaloList<TX, 8, 8> H = make_halo_list<TX, 8, 8>();
+    for (int q = 0; q < TileLayout<TX, 8, 8>::NE; q++) R.halo[q] = tp_repack<TX>(H.e[q]);
+    const FaceList<TX, 8, 8> F = make_face_list<TX, 8, 8>();
+    for (int q = 0; q < FaceList<TX, 8, 8>::N; q++) R.face[q] = tp_repack<TX>(F.e[q]);
+    return R;
+}
+template <int TX> __device__ const TpLists<TX> g_tp_lists = make_tp_lists<TX>();
+
+template <typename Real, int TX> constexpr size_t sweep_tp_smem()
+{
+    return (size_t)TpLayout<TX>::HSZ * (sizeof(typename ColT<Real>::type) + 2 * sizeof(Real));
 }
 
 // Entry column of a cell with octant indices idx at halo index h, from the
@@ -54,11 +81,11 @@ template <typename Real, int T> constexpr size_t sweep_tp_smem()
 // tied axes' interpolations are averaged.  Neighbours outside the octant are
 // dropped.  Written as weighted differences to one reference neighbour, so
 // the float-float column is not rounded to float before the increment.
-template <typename Real, int T>
+template <typename Real, int TX>
 __device__ __forceinline__ typename ColT<Real>::type
 sc_entry_general(const typename ColT<Real>::type *sN, const Real *sW, int h, const int idx[3])
 {
-    typedef TpLayout<T> L;
+    typedef TpLayout<TX> L;
     const int str[3] = {1, L::SY, L::SZ};
     const int c2[3] = {2 * idx[0] + 1, 2 * idx[1] + 1, 2 * idx[2] + 1};
     const int cm = max(c2[0], max(c2[1], c2[2]));
@@ -100,10 +127,13 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Reciprocal: correctly rounded in FP64, the fast approximation in the mixed
-// path (a few ulp; the mixed path is judged on its error against FP64).
+// Reciprocal and square root: correctly rounded in FP64, the fast
+// approximations in the mixed path (a few ulp; the mixed path is judged on its
+// error against FP64).
 __device__ __forceinline__ double tp_rcp(double a) { return 1.0 / a; }
 __device__ __forceinline__ float tp_rcp(float a) { return __fdividef(1.0f, a); }
+__device__ __forceinline__ double tp_sqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float tp_sqrt(float a) { return a * rsqrtf(a); }   // a > 0 here
 
 // Entry column of a cell with one dominant axis: bilinear weights of the
 // entry point on the upwind layer (g1 = c_t1/c_a for the t1-1 neighbour,
@@ -124,35 +154,29 @@ sc_entry_axis(const typename ColT<Real>::type *sN, const Real *sW, int h00, int 
     return ColT<Real>::add(N00, d);
 }
 
-template <typename Real, int T>
-__global__ void __launch_bounds__(T *T, sizeof(Real) == 4 ? 16 : 8) sweep_tp_kernel(SweepParams<Real> P)
+template <typename Real, int TX>
+__global__ void __launch_bounds__(64, sizeof(Real) == 4 ? (TX == 8 ? 16 : 9) : 8) sweep_tp_kernel(SweepParams<Real> P)
 {
     typedef typename ColT<Real>::type Col;
-    typedef TpLayout<T> L;
-    constexpr int NT = L::NT, NC = T * T * T, HSZ = L::HSZ;
+    typedef TpLayout<TX> L;
+    constexpr int NT = L::NT, HSZ = L::HSZ;
     constexpr int SY = L::SY, SZ = L::SZ;
-    constexpr int FMAX = T * T;
+    constexpr int FMAX = (TX * 8 > 64) ? TX * 8 : 64;   // largest face of the tile
     constexpr int NCOMP = tp_face_comps<Real>();
-    typedef TileLayout<T, T, T> HL_L;                 // layout the halo and face lists are packed for
+    constexpr int NQ = TX / 8;                          // cells per thread in a layer across x
+    static_assert(NT == 64, "64 threads: one per (j,k) column");
+    typedef TileLayout<TX, 8, 8> HL_L;                 // the packed lists' tile
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Col *sN = reinterpret_cast<Col *>(smem_raw);      // N_out
     Real *sW = reinterpret_cast<Real *>(sN + HSZ);     // 1/max(dtau, tau0); 0 outside the octant
     Real *sDI = sW + HSZ;                              // increment n x ds, then N_in
     __shared__ unsigned s_next;                        // the CTA's next ticket (claimed one tile ahead)
     __shared__ int s_bad;
-    const HaloList<T, T, T> &HL = g_halo_list<T, T, T>;
-    const FaceList<T, T, T> &FL = g_face_list<T, T, T>;
+    const TpLists<TX> &TL = g_tp_lists<TX>;
     const unsigned epoch = *(volatile unsigned *)P.epoch + 1u;
     const int tid = threadIdx.x;
-    const int tu = tid % T, tv = tid / T;              // this thread's cell within a layer or column
+    const int c8 = tid % 8, r8 = tid / 8;             // (j,k) column of this thread
 
-    // halo index of the packed halo/face list entries (packed for the pipelined layout)
-    auto remap = [](unsigned hp) {
-        const int li = (int)(hp % HL_L::SZ % HL_L::SY) - 1;
-        const int lj = (int)(hp % HL_L::SZ / HL_L::SY) - 1;
-        const int lk = (int)(hp / HL_L::SZ) - 1;
-        return L::h(li, lj, lk);
-    };
     // a ticket, marked when its grid has already reached its end time
     auto claim = [&]() {
         unsigned t = atomicAdd(P.ticket, 1u);
@@ -174,7 +198,7 @@ __global__ void __launch_bounds__(T *T, sizeof(Real) == 4 ? 16 : 8) sweep_tp_ker
         const TileItem it = P.items[tk];
         const Job J = P.jobs[it.job];
         const GridDev<Real> &G = P.grids[J.grid];
-        const int o0[3] = {it.I * T - J.off[0], it.J * T - J.off[1], it.K * T - J.off[2]};
+        const int o0[3] = {it.I * TX - J.off[0], it.J * 8 - J.off[1], it.K * 8 - J.off[2]};
         const long long tile_self = J.tile_base + ((long long)it.K * J.nt[1] + it.J) * J.nt[0] + it.I;
         const Real *xin = (P.which == 1) ? G.xh : G.x;
         const Real dx = G.dx, sig = G.sigma0, tau0 = G.tau0;
@@ -183,7 +207,7 @@ __global__ void __launch_bounds__(T *T, sizeof(Real) == 4 ? 16 : 8) sweep_tp_ker
 
         // 1. the upstream tiles (up to seven: the three face neighbours and the
         //    four edge and corner ones): wait until each has published in this
-        //    launch (bounded), then the halo is read after the barrier
+        //    launch (bounded); the halo is read after the barrier below
         if (tid == 0) s_bad = 0;
         __syncthreads();
         if (tid >= 1 && tid <= 7 && (tid & ~have) == 0) {
@@ -197,35 +221,38 @@ __global__ void __launch_bounds__(T *T, sizeof(Real) == 4 ? 16 : 8) sweep_tp_ker
                 if (ns < 256) ns <<= 1;
             }
         }
-        // 2. own cells: increments n x ds and weight factors (four loads in flight per thread)
-        for (int e0 = tid; e0 < NC; e0 += 4 * NT) {
-            long long gq[4];
-            bool in[4];
+        // 2. own cells: increments n x ds and weight factors.  Cell e = tid + 64 u
+        //    (x fastest); the global index moves by fixed strides (octant signs
+        //    folded in), four cells' loads in flight at a time.
+        const long long sxg = J.sg[0], syg = (long long)J.sg[1] * G.nx, szg = (long long)J.sg[2] * G.nx * G.ny;
+        const long long gbase = (long long)(J.sg[0] > 0 ? J.v[0] + o0[0] : J.v[0] - 1 - o0[0]) +
+                                (long long)G.nx * ((long long)(J.sg[1] > 0 ? J.v[1] + o0[1] : J.v[1] - 1 - o0[1]) +
+                                                   (long long)G.ny * (J.sg[2] > 0 ? J.v[2] + o0[2] : J.v[2] - 1 - o0[2]));
+        const int i_lo = max(-o0[0], 0), i_hi = min(J.ext[0] - o0[0], TX);   // in-octant local ranges
+        const int j_lo = max(-o0[1], 0), j_hi = min(J.ext[1] - o0[1], 8);
+        const int k_lo = max(-o0[2], 0), k_hi = min(J.ext[2] - o0[2], 8);
+#pragma unroll
+        for (int b = 0; b < TX; b += 4) {
             Real nv[4], xv[4];
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                const int e = e0 + u * NT;
-                const int li = e % T, lj = (e / T) % T, lk = e / (T * T);
-                const int i = o0[0] + li, j = o0[1] + lj, k = o0[2] + lk;
-                in[u] = e < NC && i >= 0 && j >= 0 && k >= 0 && i < J.ext[0] && j < J.ext[1] && k < J.ext[2];
-                const int X = J.sg[0] > 0 ? J.v[0] + i : J.v[0] - 1 - i;
-                const int Y = J.sg[1] > 0 ? J.v[1] + j : J.v[1] - 1 - j;
-                const int Z = J.sg[2] > 0 ? J.v[2] + k : J.v[2] - 1 - k;
-                gq[u] = (long long)X + (long long)G.nx * ((long long)Y + (long long)G.ny * Z);
-                nv[u] = in[u] ? (G.n ? __ldg(G.n + gq[u]) : G.n_uniform) : Real(0);
-                xv[u] = in[u] ? __ldg(xin + gq[u]) : Real(0);
+                const int e = tid + 64 * (b + u);
+                const int li = e % TX, lj = (e / TX) % 8, lk = e / (TX * 8);
+                const bool in = li >= i_lo && li < i_hi && lj >= j_lo && lj < j_hi && lk >= k_lo && lk < k_hi;
+                const long long gq = gbase + li * sxg + lj * syg + lk * szg;
+                nv[u] = in ? (G.n ? __ldg(G.n + gq) : G.n_uniform) : Real(0);
+                xv[u] = in ? __ldg(xin + gq) : Real(0);
             }
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                const int e = e0 + u * NT;
-                if (e >= NC) continue;
-                const int li = e % T, lj = (e / T) % T, lk = e / (T * T);
+                const int e = tid + 64 * (b + u);
+                const int li = e % TX, lj = (e / TX) % 8, lk = e / (TX * 8);
                 const int h = L::h(li, lj, lk);
                 Real dN = Real(0), wf = Real(0);
-                if (in[u]) {
+                if (li >= i_lo && li < i_hi && lj >= j_lo && lj < j_hi && lk >= k_lo && lk < k_hi) {
                     const Real c0 = Real(o0[0] + li) + Real(0.5), c1 = Real(o0[1] + lj) + Real(0.5),
                                c2 = Real(o0[2] + lk) + Real(0.5);
-                    const Real ds = dx * m_sqrt(c0 * c0 + c1 * c1 + c2 * c2) * tp_rcp(m_max(c0, m_max(c1, c2)));
+                    const Real ds = dx * tp_sqrt(c0 * c0 + c1 * c1 + c2 * c2) * tp_rcp(m_max(c0, m_max(c1, c2)));
                     dN = nv[u] * xv[u] * ds;
                     wf = tp_rcp(m_max(sig * dN, tau0));
                 }
@@ -238,9 +265,9 @@ __global__ void __launch_bounds__(T *T, sizeof(Real) == 4 ? 16 : 8) sweep_tp_ker
         // 3. the halo from the upstream tiles' published faces (read past L1)
         const bool bad = s_bad != 0;
         for (int q = tid; q < HL_L::NE; q += NT) {
-            const unsigned en = __ldg(&HL.e[q]);
+            const unsigned en = __ldg(&TL.halo[q]);
             const unsigned mask = en >> 28;
-            const int h = remap(en & 0x3fffu);
+            const int h = (int)(en & 0x3fffu);
             Col vN = ColT<Real>::zero();
             Real vW = Real(0);
             if ((mask & ~have) == 0 && !bad) {
@@ -262,39 +289,59 @@ __global__ void __launch_bounds__(T *T, sizeof(Real) == 4 ? 16 : 8) sweep_tp_ker
         __syncthreads();
 
         // 4. one dominant axis over the whole tile (in-octant cells), or mixed
-        const int lo0 = max(o0[0], 0), lo1 = max(o0[1], 0), lo2 = max(o0[2], 0);
-        const int hi0 = min(o0[0] + T, J.ext[0]) - 1, hi1 = min(o0[1] + T, J.ext[1]) - 1,
-                  hi2 = min(o0[2] + T, J.ext[2]) - 1;
+        const int lo0 = o0[0] + i_lo, lo1 = o0[1] + j_lo, lo2 = o0[2] + k_lo;
+        const int hi0 = o0[0] + i_hi - 1, hi1 = o0[1] + j_hi - 1, hi2 = o0[2] + k_hi - 1;
         int pure = -1;
         if (lo0 > hi1 && lo0 > hi2) pure = 0;
         else if (lo1 > hi0 && lo1 > hi2) pure = 1;
         else if (lo2 > hi0 && lo2 > hi1) pure = 2;
 
-        if (pure >= 0) {
-            // layer by layer along the dominant axis a, with transverse axes
-            // t1 = a+1, t2 = a+2 (mod 3); this thread's cell of each layer sits
-            // at (lj, lk) = (tu, tv) for a = 0, (li, lk) for a = 1, (li, lj) for a = 2
-            const int a = pure;
-            const int h0 = a == 0 ? L::h(0, tu, tv) : (a == 1 ? L::h(tu, 0, tv) : L::h(tu, tv, 0));
-            const int sa = a == 0 ? 1 : (a == 1 ? SY : SZ);
-            const int s1 = a == 0 ? SY : (a == 1 ? SZ : 1);
-            const int s2 = a == 0 ? SZ : (a == 1 ? 1 : SY);
-            const int idx1 = a == 0 ? o0[1] + tu : (a == 1 ? o0[2] + tv : o0[0] + tu);
-            const int idx2 = a == 0 ? o0[2] + tv : (a == 1 ? o0[0] + tu : o0[1] + tv);
-            const int ext1 = a == 0 ? J.ext[1] : (a == 1 ? J.ext[2] : J.ext[0]);
-            const int ext2 = a == 0 ? J.ext[2] : (a == 1 ? J.ext[0] : J.ext[1]);
-            const int oa = a == 0 ? o0[0] : (a == 1 ? o0[1] : o0[2]);
-            const int exta = a == 0 ? J.ext[0] : (a == 1 ? J.ext[1] : J.ext[2]);
-            const bool col_in = idx1 >= 0 && idx2 >= 0 && idx1 < ext1 && idx2 < ext2;
-            const Real c1 = Real(2 * idx1 + 1), c2 = Real(2 * idx2 + 1);
-            for (int l = 0; l < T; l++) {
-                const int ia = oa + l;
-                if (col_in && ia >= 0 && ia < exta) {
-                    const int h = h0 + l * sa;
-                    const Real ica = tp_rcp(Real(2 * ia + 1));
-                    const Col Nin = sc_entry_axis<Real>(sN, sW, h - sa, s1, s2, c1 * ica, c2 * ica);
+        if (pure == 0) {
+            // layers along x: this thread's cell (l, lj, lk) = (l, c8, r8)
+            const int lj = c8, lk = r8;
+            const bool col_in = lj >= j_lo && lj < j_hi && lk >= k_lo && lk < k_hi;
+            const Real c1 = Real(2 * (o0[1] + lj) + 1), c2 = Real(2 * (o0[2] + lk) + 1);
+            for (int l = 0; l < TX; l++) {
+                if (col_in && l >= i_lo && l < i_hi) {
+                    const int h = L::h(l, lj, lk);
+                    const Real ica = tp_rcp(Real(2 * (o0[0] + l) + 1));
+                    const Col Nin = sc_entry_axis<Real>(sN, sW, h - 1, SY, SZ, c1 * ica, c2 * ica);
                     sN[h] = ColT<Real>::add(Nin, sDI[h]);
                     sDI[h] = ColT<Real>::to_real(Nin);
+                }
+                __syncthreads();
+            }
+        } else if (pure > 0) {
+            // layers along y (a = 1; transverse t1 = z, t2 = x) or z (a = 2; t1 = x,
+            // t2 = y): this thread's cells (li, lb) with lb the other transverse
+            // index, li = tid % TX and lb = tid / TX + q 64/TX
+            const int a = pure;
+            const int sa = a == 1 ? SY : SZ;
+            const int s1 = a == 1 ? SZ : 1;
+            const int s2 = a == 1 ? 1 : SY;
+            const int oa = a == 1 ? o0[1] : o0[2];
+            const int la_lo = a == 1 ? j_lo : k_lo, la_hi = a == 1 ? j_hi : k_hi;
+            const int ob = a == 1 ? o0[2] : o0[1];               // the other transverse axis
+            const int lb_lo = a == 1 ? k_lo : j_lo, lb_hi = a == 1 ? k_hi : j_hi;
+            const int li = tid % TX;
+            const bool i_in = li >= i_lo && li < i_hi;
+            const Real cx = Real(2 * (o0[0] + li) + 1);
+            for (int l = 0; l < 8; l++) {
+                if (l >= la_lo && l < la_hi && i_in) {
+                    const Real ica = tp_rcp(Real(2 * (oa + l) + 1));
+#pragma unroll
+                    for (int q = 0; q < NQ; q++) {
+                        const int lb = tid / TX + q * (64 / TX);
+                        if (lb >= lb_lo && lb < lb_hi) {
+                            const int h = a == 1 ? L::h(li, l, lb) : L::h(li, lb, l);
+                            const Real cb = Real(2 * (ob + lb) + 1);
+                            // a = 1: g1 for the z-1 neighbour, g2 for x-1; a = 2: g1 for x-1, g2 for y-1
+                            const Real g1 = (a == 1 ? cb : cx) * ica, g2 = (a == 1 ? cx : cb) * ica;
+                            const Col Nin = sc_entry_axis<Real>(sN, sW, h - sa, s1, s2, g1, g2);
+                            sN[h] = ColT<Real>::add(Nin, sDI[h]);
+                            sDI[h] = ColT<Real>::to_real(Nin);
+                        }
+                    }
                 }
                 __syncthreads();
             }
@@ -302,14 +349,13 @@ __global__ void __launch_bounds__(T *T, sizeof(Real) == 4 ? 16 : 8) sweep_tp_ker
             // plane by plane (li + lj + lk = m), one thread per (lj, lk) column;
             // cells with one dominant axis take the cheap form, tied cells the
             // average over their tied axes, the vertex cell N_in = 0
-            const int lj = tu, lk = tv;
+            const int lj = c8, lk = r8;
             const int j = o0[1] + lj, k = o0[2] + lk;
-            const bool col_in = j >= 0 && k >= 0 && j < J.ext[1] && k < J.ext[2];
-            const int m_lo = lj + lk, m_hi = lj + lk + T - 1;
+            const bool col_in = lj >= j_lo && lj < j_hi && lk >= k_lo && lk < k_hi;
             for (int m = 0; m < L::NP; m++) {
                 const int li = m - lj - lk;
-                const int i = o0[0] + li;
-                if (col_in && m >= m_lo && m <= m_hi && i >= 0 && i < J.ext[0]) {
+                if (col_in && li >= i_lo && li < i_hi) {
+                    const int i = o0[0] + li;
                     const int h = L::h(li, lj, lk);
                     const int c2i = 2 * i + 1, c2j = 2 * j + 1, c2k = 2 * k + 1;
                     const int cm = max(c2i, max(c2j, c2k));
@@ -326,7 +372,7 @@ __global__ void __launch_bounds__(T *T, sizeof(Real) == 4 ? 16 : 8) sweep_tp_ker
                         Nin = sc_entry_axis<Real>(sN, sW, h - sa, s1, s2, Real(ct1) * ica, Real(ct2) * ica);
                     } else {
                         const int idx[3] = {i, j, k};
-                        Nin = sc_entry_general<Real, T>(sN, sW, h, idx);
+                        Nin = sc_entry_general<Real, TX>(sN, sW, h, idx);
                     }
                     sN[h] = ColT<Real>::add(Nin, sDI[h]);
                     sDI[h] = ColT<Real>::to_real(Nin);
@@ -337,21 +383,18 @@ __global__ void __launch_bounds__(T *T, sizeof(Real) == 4 ? 16 : 8) sweep_tp_ker
 
         // 5. entry columns of the tile's cells, then its downstream faces and flag
         Real *Nout = (P.which == 1 ? G.N2 : G.N1) + (long long)J.src * G.ncell;
-        for (int e = tid; e < NC; e += NT) {
-            const int li = e % T, lj = (e / T) % T, lk = e / (T * T);
-            const int i = o0[0] + li, j = o0[1] + lj, k = o0[2] + lk;
-            if (i >= 0 && j >= 0 && k >= 0 && i < J.ext[0] && j < J.ext[1] && k < J.ext[2]) {
-                const int X = J.sg[0] > 0 ? J.v[0] + i : J.v[0] - 1 - i;
-                const int Y = J.sg[1] > 0 ? J.v[1] + j : J.v[1] - 1 - j;
-                const int Z = J.sg[2] > 0 ? J.v[2] + k : J.v[2] - 1 - k;
-                Nout[(long long)X + (long long)G.nx * ((long long)Y + (long long)G.ny * Z)] = sDI[L::h(li, lj, lk)];
-            }
+#pragma unroll 4
+        for (int u = 0; u < TX; u++) {
+            const int e = tid + 64 * u;
+            const int li = e % TX, lj = (e / TX) % 8, lk = e / (TX * 8);
+            if (li >= i_lo && li < i_hi && lj >= j_lo && lj < j_hi && lk >= k_lo && lk < k_hi)
+                Nout[gbase + li * sxg + lj * syg + lk * szg] = sDI[L::h(li, lj, lk)];
         }
         if (tile_self != P.skip_publish) {
             Real *fbase = P.tpfaces + tile_self * 3 * NCOMP * FMAX;
-            for (int q = tid; q < FaceList<T, T, T>::N; q += NT) {
-                const unsigned en = __ldg(&FL.e[q]);
-                const int h = remap(en & 0x3fffu);
+            for (int q = tid; q < FaceList<TX, 8, 8>::N; q += NT) {
+                const unsigned en = __ldg(&TL.face[q]);
+                const int h = (int)(en & 0x3fffu);
                 Real *f = fbase + ((en >> 26) & 3u) * NCOMP * FMAX + ((en >> 14) & 0xfffu);
                 const Col v = sN[h];
                 if (sizeof(Real) == 4) {

@@ -26,7 +26,7 @@ def _rel(a, b, floor=1.0):
 
 
 # --------------------------------------------------------------------------- trace
-@pytest.mark.parametrize("shape", range(8))
+@pytest.mark.parametrize("shape", range(9))
 def test_trace_columns_every_tile_shape(shape):
     """Ragged non-cubic grid, two sources (one on the grid corner vertex),
     every tile shape: columns equal the oracle's to 1e-12 relative."""

@@ -13,7 +13,8 @@ import oracle
 from paper_1201_5651_gb300 import inputs, oots
 
 pytestmark = pytest.mark.gpu
-TP = 7
+TP = 7          # 8 x 8 x 8 tiles
+TP16 = 8        # 16 x 8 x 8 tiles
 XTOL = 1e-9
 
 
@@ -29,8 +30,9 @@ def _three_sources(seed=5, n=41, ny=33, nz=29, spectrum="mono"):
     return w
 
 
+@pytest.mark.parametrize("tp", [TP, TP16])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-5)])
-def test_tp_columns_match_the_oracle(precision, tol):
+def test_tp_columns_match_the_oracle(precision, tol, tp):
     """FP64: the oracle's columns to 1e-12.  Mixed (float density, state and
     weights, float-float columns): within 1e-5 over paths of ~60 cells, and no
     further from the oracle than the pipelined kernel's columns (plus 1e-7)."""
@@ -38,14 +40,14 @@ def test_tp_columns_match_the_oracle(precision, tol):
     P = oracle.Problem.from_workload(w)
     ref = [P.trace(s, w.x0) for s in range(3)]
     err = {}
-    for shape in (0, TP):
+    for shape in (0, tp):
         c = oots.Context.from_workload(w, precision, scheme=oots.OOTS_A3, K4=0.25)
         c.set_tile_shape(shape)
         c.compute_dt()
         err[shape] = [_rel(c.get_column_density(s), ref[s]) for s in range(3)]
     for s in range(3):
-        assert err[TP][s] <= tol, (precision, s, err)
-        assert err[TP][s] <= 2.0 * err[0][s] + 1e-7, (precision, s, err)
+        assert err[tp][s] <= tol, (precision, s, err)
+        assert err[tp][s] <= 2.0 * err[0][s] + 1e-7, (precision, s, err)
 
 
 def test_tp_columns_partially_ionised_state_fp64():
@@ -58,23 +60,25 @@ def test_tp_columns_partially_ionised_state_fp64():
     P = oracle.Problem.from_workload(w)
     ref = [P.trace(s, w.x0) for s in range(3)]
     err = {}
-    for shape in (0, TP):
+    for shape in (0, TP, TP16):
         c = oots.Context.from_workload(w, "fp64", scheme=oots.OOTS_A3, K4=0.25)
         c.set_tile_shape(shape)
         c.compute_dt()
         err[shape] = [_rel(c.get_column_density(s), ref[s]) for s in range(3)]
     for s in range(3):
-        assert err[TP][s] <= 1e-10, (s, err)
-        assert err[TP][s] <= 4.0 * err[0][s] + 1e-13, (s, err)
+        for tp in (TP, TP16):
+            assert err[tp][s] <= 1e-10, (s, tp, err)
+            assert err[tp][s] <= 4.0 * err[0][s] + 1e-13, (s, tp, err)
 
 
+@pytest.mark.parametrize("tp", [TP, TP16])
 @pytest.mark.parametrize("scheme", [2, 3])
-def test_tp_adaptive_substeps_fp64(scheme):
+def test_tp_adaptive_substeps_fp64(scheme, tp):
     """A2 and A3 with Eq. 4 (K4 = 1/4) on the throughput sweep: the step and every
     cell's neutral fraction follow the oracle for three substeps (both traces of A3)."""
     w = _three_sources(seed=21, spectrum="bb")
     c = oots.Context.from_workload(w, "fp64", scheme=scheme, K4=0.25)
-    c.set_tile_shape(TP)
+    c.set_tile_shape(tp)
     P = oracle.Problem.from_workload(w)
     x = np.ascontiguousarray(w.x0.astype(np.float64))
     t = 0.0
@@ -87,13 +91,14 @@ def test_tp_adaptive_substeps_fp64(scheme):
         assert float(np.max(np.abs(c.get_neutral_fraction() - x))) <= XTOL, (scheme, k)
 
 
-def test_tp_shape_runs_A1_on_the_pipelined_kernel():
+@pytest.mark.parametrize("tp", [TP, TP16])
+def test_tp_shape_runs_A1_on_the_pipelined_kernel(tp):
     """The implicit sweep (A1) integrates on the chain; with shape 7 it runs the
     pipelined kernel on the same 8^3 tiles and still follows the oracle."""
     w = inputs.small_random(n=19, ny=17, nz=15, seed=4, nsrc=1)
     dt = 0.05 * w.t_rec
     c = oots.Context.from_workload(w, "fp64", scheme=oots.OOTS_A1, dt_fixed=dt)
-    c.set_tile_shape(TP)
+    c.set_tile_shape(tp)
     c.step(dt)
     P = oracle.Problem.from_workload(w)
     x = np.ascontiguousarray(w.x0.astype(np.float64))
@@ -106,11 +111,26 @@ def test_tp_many_sources_advance_mixed_matches_pipelined():
     throughput and pipelined sweeps agree on the front (ionised volume) and per cell."""
     w = inputs.multisource(40, 1.0, 1205, nsrc=16, box_rs=2.0)
     out = []
-    for shape in (0, TP):
+    for shape in (0, TP, TP16):
         c = oots.Context.from_workload(w, "mixed", scheme=3, K4=0.25)
         c.set_tile_shape(shape)
         c.advance(0.02 * w.t_rec)
         out.append(c.get_neutral_fraction())
-    v0, v1 = float((1 - out[0]).sum()), float((1 - out[1]).sum())
-    assert abs(v1 / v0 - 1.0) <= 1e-4
-    assert float(np.abs(out[0] - out[1]).max()) <= 1e-3
+    v0 = float((1 - out[0]).sum())
+    for o in out[1:]:
+        assert abs(float((1 - o).sum()) / v0 - 1.0) <= 1e-4
+        assert float(np.abs(out[0] - o).max()) <= 1e-3
+
+
+@pytest.mark.parametrize("shape", [0, 4, TP, TP16])
+def test_octant_aligned_tiles_match_the_oracle(shape):
+    """Tiles started at each octant's origin (tuning key 4) instead of at global
+    multiples of the tile size: the same columns, to 1e-12 (FP64)."""
+    w = _three_sources(seed=13)
+    c = oots.Context.from_workload(w, "fp64", scheme=oots.OOTS_A3, K4=0.25)
+    c.set_tile_shape(shape)
+    c.debug_set(4, 1)
+    c.compute_dt()
+    P = oracle.Problem.from_workload(w)
+    for s in range(3):
+        assert _rel(c.get_column_density(s), P.trace(s, w.x0)) <= 1e-12, (shape, s)
