@@ -60,6 +60,11 @@ template <typename Real> int sweep_occupancy(int shape, int mode);   // resident
 template <typename Real> bool sweep_shape_ok(int shape);              // fits the shared memory of this device
 template <typename Real>
 cudaError_t launch_sweep(const SweepParams<Real> &P, int shape, int mode, int nblocks, cudaStream_t s);
+// n x of the traced state (which = 0: x, 1: xh) into each grid's bricks (GridDev::nxb) for the
+// throughput kernel of tile shape `shape`; max_elems = the largest grid's brick cells
+template <typename Real>
+cudaError_t launch_pack_nx(const GridDev<Real> *grids, int ngrid, int which, int shape, long long max_elems, int nsm,
+                           cudaStream_t s);
 
 // Plane-parallel sources: which = 0 traces x into N1, 1 traces xh into N2;
 // implicit = 1 runs the A1 row integration instead (single source).  The jobs

@@ -154,6 +154,8 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     unsigned long long *d_faces = nullptr;
     Real *d_tpfaces = nullptr;         // throughput sweep: untagged faces, and a flag per tile
     unsigned *d_tpflags = nullptr;
+    std::vector<void *> brickmem;      // throughput sweep: per grid n x in bricks of the tile
+    long long brick_max = 0;           // brick cells of the largest grid (0: no bricks)
     PlaneJob *d_pjobs = nullptr;       // plane-parallel sources
     int npjobs = 0, nrow0 = 0;         // jobs; of them, rows along x (first in the array)
     long long plane_threads = 0, threads0 = 0;
@@ -190,6 +192,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         cudaFree(d_pjobs);
         cudaFree(d_tabs);
         for (void *p : tabmem) cudaFree(p);
+        for (void *p : brickmem) cudaFree(p);
         cudaFree(d_offsets);
         cudaFree(d_queue);
         cudaFree(d_qrec);
@@ -347,6 +350,23 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         });
 
         CU(cudaSetDevice(device));
+        // bricks of n x for the throughput kernel's traces (tiles at global multiples of the tile only)
+        if (is_tp_shape(shape) && scheme != OOTS_A1 && !jobs.empty()) {
+            for (size_t g = 0; g < cs.size(); g++) {
+                oots_ctx *c = cs[g];
+                if (c->tile_align) continue;
+                GridDev<Real> &G = grids[g];
+                G.nbx = (c->nx + TX - 1) / TX;
+                G.nby = (c->ny + TY - 1) / TY;
+                G.nbz = (c->nz + TZ - 1) / TZ;
+                const long long cells = (long long)G.nbx * G.nby * G.nbz * TX * TY * TZ;
+                void *p = nullptr;
+                CU(cudaMalloc(&p, (size_t)cells * sizeof(Real)));
+                brickmem.push_back(p);
+                G.nxb = (Real *)p;
+                brick_max = std::max(brick_max, cells);
+            }
+        }
         if (nsmax > 1) {
             // no threshold until the first step sets them (+inf: every source is looked at)
             const size_t nn = grids.size() * 3 * MAX_SRC;
@@ -442,6 +462,9 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         if (nitems > 0) {
             CU(cudaMemsetAsync(d_sync, 0, 2 * sizeof(unsigned), s));   // ticket and done; the epoch persists
             if (prof) prof->mark(0);
+            // the trace's input in bricks (timed with the trace)
+            if (mode == 0 && brick_max > 0)
+                CU(launch_pack_nx<Real>(d_grids, (int)ctxs.size(), which, shape, brick_max, ctxs[0]->nsm, s));
             CU(launch_sweep<Real>(params(which), shape, mode, mode == 0 ? nblocks0 : nblocks1, s));
             if (prof) prof->mark(mode == 1 ? OOTS_K_IMPLICIT : (which == 0 ? OOTS_K_SWEEP1 : OOTS_K_SWEEP2));
         }

@@ -76,6 +76,10 @@ template <typename Real> struct GridDev {
     int tab[MAX_SRC];         // -1 monochromatic, else table index
     unsigned char pcode[MAX_SRC];  // 0: vertex point source; 1 + 2*axis + back: plane source (qfac = F/dx)
     float lnamp0[MAX_SRC];    // ln(qfac sigma0 dx): a source's largest rate per unit x is qfac sigma0 dx p / r2
+    Real *nxb;                // n x of the traced state in bricks of the throughput tile (nullptr: none):
+                              // brick (bx, by, bz) of nbx x nby x nbz holds cells bx*TX.., by*8.., bz*8..,
+                              // x fastest, TX = the tile's x extent
+    int nbx, nby, nbz;
     Real *nstar;              // 3 x MAX_SRC entry columns beyond which a source cannot matter for the
                               // dt pass (step hint), the half step and the full step (nullptr: none)
     DevState *st;

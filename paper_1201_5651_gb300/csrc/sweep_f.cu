@@ -8,4 +8,5 @@ template bool sweep_shape_ok<float>(int);
 template int sweep_occupancy<float>(int, int);
 template cudaError_t prepare_sweeps<float>();
 template cudaError_t launch_sweep<float>(const SweepParams<float> &, int, int, int, cudaStream_t);
+template cudaError_t launch_pack_nx<float>(const GridDev<float> *, int, int, int, long long, int, cudaStream_t);
 } // namespace oots

@@ -844,6 +844,21 @@ cudaError_t launch_sweep(const SweepParams<Real> &P, int shape, int mode, int nb
 }
 
 template <typename Real>
+cudaError_t launch_pack_nx(const GridDev<Real> *grids, int ngrid, int which, int shape, long long max_elems, int nsm,
+                           cudaStream_t s)
+{
+    if (ngrid <= 0 || max_elems <= 0) return cudaSuccess;
+    if (ngrid > 65535) return cudaErrorInvalidValue;
+    long long nb = (max_elems + 255) / 256;
+    const long long cap = (long long)(nsm > 0 ? nsm : 1) * 8;       // 2048 threads per SM
+    if (nb > cap) nb = cap;
+    const dim3 grid((unsigned)nb, (unsigned)ngrid);
+    if (shape == SHAPE_TP16) pack_nx_kernel<Real, 16><<<grid, 256, 0, s>>>(grids, which);
+    else pack_nx_kernel<Real, 8><<<grid, 256, 0, s>>>(grids, which);
+    return cudaGetLastError();
+}
+
+template <typename Real>
 cudaError_t prepare_sweeps()
 {
     cudaError_t e = cudaSuccess, e2;

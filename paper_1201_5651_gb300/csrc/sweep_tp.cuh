@@ -45,8 +45,11 @@ template <int TX> struct TpLayout {
     static_assert(HSZ < (1 << 14), "halo entry packing");
 };
 
-// The halo and face lists of a tile (built for the pipelined layout),
-// repacked with the throughput layout's shared-memory index in the low 14 bits.
+// The halo and face lists of a tile in the pipelined kernel's packing, with
+// the throughput layout's shared-memory index in the low 14 bits.  Unlike the
+// pipelined kernel's lists (sorted by the plane that first needs an entry),
+// these keep the faces' own order, so that a warp's 32 entries are adjacent
+// in the published face and its loads and stores touch whole sectors.
 template <int TX> struct TpLists {
     unsigned halo[TileLayout<TX, 8, 8>::NE];
     unsigned face[FaceList<TX, 8, 8>::N];
@@ -61,10 +64,16 @@ template <int TX> constexpr unsigned tp_repack(unsigned e)
 template <int TX> constexpr TpLists<TX> make_tp_lists()
 {
     TpLists<TX> R{};
-    const HaloList<TX, 8, 8> H = make_halo_list<TX, 8, 8>();
-    for (int q = 0; q < TileLayout<TX, 8, 8>::NE; q++) R.halo[q] = tp_repack<TX>(H.e[q]);
-    const FaceList<TX, 8, 8> F = make_face_list<TX, 8, 8>();
-    for (int q = 0; q < FaceList<TX, 8, 8>::N; q++) R.face[q] = tp_repack<TX>(F.e[q]);
+    for (int q = 0; q < TileLayout<TX, 8, 8>::NE; q++) {
+        int key = 0; unsigned p = 0;
+        halo_entry<TX, 8, 8>(q, key, p);
+        R.halo[q] = tp_repack<TX>(p);
+    }
+    for (int q = 0; q < FaceList<TX, 8, 8>::N; q++) {
+        int key = 0; unsigned p = 0;
+        face_entry<TX, 8, 8>(q, key, p);
+        R.face[q] = tp_repack<TX>(p);
+    }
     return R;
 }
 template <int TX> __device__ const TpLists<TX> g_tp_lists = make_tp_lists<TX>();
@@ -154,6 +163,53 @@ sc_entry_axis(const typename ColT<Real>::type *sN, const Real *sW, int h00, int 
     return ColT<Real>::add(N00, d);
 }
 
+// The trace's input n x (density times neutral fraction of the traced state)
+// in bricks of TX x 8 x 8 cells, x fastest within a brick and bricks x
+// fastest (zero outside the grid).  Tiles start at global multiples of the
+// tile, so each tile of each octant lies in one brick and reads its cells as
+// one contiguous block, where the grid's own layout gives it 64 rows of TX
+// cells in two arrays.  The product is rounded as the sweep would round it.
+// One row of blocks per grid (blockIdx.y).
+template <typename Real, int TX>
+__global__ void __launch_bounds__(256) pack_nx_kernel(const GridDev<Real> *grids, int which)
+{
+    const GridDev<Real> &G = grids[blockIdx.y];
+    Real *B = G.nxb;
+    if (B == nullptr) return;
+    constexpr unsigned NC = TX * 64u;
+    const Real *xs = which == 1 ? G.xh : G.x;
+    const Real *n = G.n;
+    const Real nu = G.n_uniform;
+    const unsigned nbx = (unsigned)G.nbx, nbxy = (unsigned)G.nbx * (unsigned)G.nby;
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const long long total = (long long)nbxy * (unsigned)G.nbz * NC;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const unsigned b = (unsigned)(q / NC), e = (unsigned)(q % NC);
+        const int gi = (int)(b % nbx) * TX + (int)(e % TX);
+        const int gj = (int)(b % nbxy / nbx) * 8 + (int)(e / TX % 8);
+        const int gk = (int)(b / nbxy) * 8 + (int)(e / (TX * 8));
+        Real v = Real(0);
+        if (gi < nx && gj < ny && gk < nz) {
+            const long long g = gi + (long long)nx * (gj + (long long)ny * gk);
+            v = (n ? __ldg(n + g) : nu) * __ldg(xs + g);
+        }
+        B[q] = v;
+    }
+}
+
+// four consecutive values (16-byte aligned for float, 32 for double)
+__device__ __forceinline__ void tp_load4(const float *p, float v[4])
+{
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void tp_load4(const double *p, double v[4])
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p)), b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
 template <typename Real, int TX>
 __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? (TX == 8 ? 16 : 9) : 8) sweep_tp_kernel(SweepParams<Real> P)
 {
@@ -231,34 +287,70 @@ __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? (TX == 8 ? 16 : 9) : 8
         const int i_lo = max(-o0[0], 0), i_hi = min(J.ext[0] - o0[0], TX);   // in-octant local ranges
         const int j_lo = max(-o0[1], 0), j_hi = min(J.ext[1] - o0[1], 8);
         const int k_lo = max(-o0[2], 0), k_hi = min(J.ext[2] - o0[2], 8);
+        if (G.nxb != nullptr) {
+            // the tile's brick: its lowest global cell along each axis is a
+            // multiple of the tile; thread tid takes brick cells 4 (tid + 64 v) ..+3
+            const int lo0 = J.sg[0] > 0 ? J.v[0] + o0[0] : J.v[0] - o0[0] - TX;
+            const int lo1 = J.sg[1] > 0 ? J.v[1] + o0[1] : J.v[1] - o0[1] - 8;
+            const int lo2 = J.sg[2] > 0 ? J.v[2] + o0[2] : J.v[2] - o0[2] - 8;
+            const Real *brick =
+                G.nxb + ((long long)((lo2 / 8) * G.nby + lo1 / 8) * G.nbx + lo0 / TX) * (long long)L::NC;
 #pragma unroll
-        for (int b = 0; b < TX; b += 4) {
-            Real nv[4], xv[4];
+            for (int v = 0; v < L::NC / 256; v++) {
+                const int e0 = 4 * (tid + 64 * v);
+                const int bj = (e0 / TX) % 8, bk = e0 / (TX * 8);
+                const int lj = J.sg[1] > 0 ? bj : 7 - bj, lk = J.sg[2] > 0 ? bk : 7 - bk;
+                const bool row_in = lj >= j_lo && lj < j_hi && lk >= k_lo && lk < k_hi;
+                Real nxv[4];
+                if (row_in) tp_load4(brick + e0, nxv);
 #pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int e = tid + 64 * (b + u);
-                const int li = e % TX, lj = (e / TX) % 8, lk = e / (TX * 8);
-                const bool in = li >= i_lo && li < i_hi && lj >= j_lo && lj < j_hi && lk >= k_lo && lk < k_hi;
-                const long long gq = gbase + li * sxg + lj * syg + lk * szg;
-                nv[u] = in ? (G.n ? __ldg(G.n + gq) : G.n_uniform) : Real(0);
-                xv[u] = in ? __ldg(xin + gq) : Real(0);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const int e = tid + 64 * (b + u);
-                const int li = e % TX, lj = (e / TX) % 8, lk = e / (TX * 8);
-                const int h = L::h(li, lj, lk);
-                Real dN = Real(0), wf = Real(0);
-                if (li >= i_lo && li < i_hi && lj >= j_lo && lj < j_hi && lk >= k_lo && lk < k_hi) {
-                    const Real c0 = Real(o0[0] + li) + Real(0.5), c1 = Real(o0[1] + lj) + Real(0.5),
-                               c2 = Real(o0[2] + lk) + Real(0.5);
-                    const Real ds = dx * tp_sqrt(c0 * c0 + c1 * c1 + c2 * c2) * tp_rcp(m_max(c0, m_max(c1, c2)));
-                    dN = nv[u] * xv[u] * ds;
-                    wf = tp_rcp(m_max(sig * dN, tau0));
+                for (int c = 0; c < 4; c++) {
+                    const int bi = e0 % TX + c;
+                    const int li = J.sg[0] > 0 ? bi : TX - 1 - bi;
+                    const int h = L::h(li, lj, lk);
+                    Real dN = Real(0), wf = Real(0);
+                    if (row_in && li >= i_lo && li < i_hi) {
+                        const Real c0 = Real(o0[0] + li) + Real(0.5), c1 = Real(o0[1] + lj) + Real(0.5),
+                                   c2 = Real(o0[2] + lk) + Real(0.5);
+                        const Real ds = dx * tp_sqrt(c0 * c0 + c1 * c1 + c2 * c2) * tp_rcp(m_max(c0, m_max(c1, c2)));
+                        dN = nxv[c] * ds;
+                        wf = tp_rcp(m_max(sig * dN, tau0));
+                    }
+                    sN[h] = ColT<Real>::zero();
+                    sW[h] = wf;
+                    sDI[h] = dN;
                 }
-                sN[h] = ColT<Real>::zero();
-                sW[h] = wf;
-                sDI[h] = dN;
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < TX; b += 4) {
+                Real nv[4], xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int e = tid + 64 * (b + u);
+                    const int li = e % TX, lj = (e / TX) % 8, lk = e / (TX * 8);
+                    const bool in = li >= i_lo && li < i_hi && lj >= j_lo && lj < j_hi && lk >= k_lo && lk < k_hi;
+                    const long long gq = gbase + li * sxg + lj * syg + lk * szg;
+                    nv[u] = in ? (G.n ? __ldg(G.n + gq) : G.n_uniform) : Real(0);
+                    xv[u] = in ? __ldg(xin + gq) : Real(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int e = tid + 64 * (b + u);
+                    const int li = e % TX, lj = (e / TX) % 8, lk = e / (TX * 8);
+                    const int h = L::h(li, lj, lk);
+                    Real dN = Real(0), wf = Real(0);
+                    if (li >= i_lo && li < i_hi && lj >= j_lo && lj < j_hi && lk >= k_lo && lk < k_hi) {
+                        const Real c0 = Real(o0[0] + li) + Real(0.5), c1 = Real(o0[1] + lj) + Real(0.5),
+                                   c2 = Real(o0[2] + lk) + Real(0.5);
+                        const Real ds = dx * tp_sqrt(c0 * c0 + c1 * c1 + c2 * c2) * tp_rcp(m_max(c0, m_max(c1, c2)));
+                        dN = nv[u] * xv[u] * ds;
+                        wf = tp_rcp(m_max(sig * dN, tau0));
+                    }
+                    sN[h] = ColT<Real>::zero();
+                    sW[h] = wf;
+                    sDI[h] = dN;
+                }
             }
         }
         __syncthreads();
