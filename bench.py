@@ -213,8 +213,8 @@ def _traffic(workload, kinds, tile_shape):
             except ValueError:
                 shape = None
         cells = [c.strip().strip("`") for c in line.strip().strip("|").split("|")]
-        if len(cells) >= 3 and cells[0] in ("sweep1", "ratedt", "half", "half_general", "sweep2", "full",
-                                            "full_general"):
+        if len(cells) >= 3 and cells[0] in ("pack", "sweep1", "ratedt", "ratedt_verify", "half", "half_general",
+                                            "sweep2", "full", "full_general"):
             try:
                 rows[cells[0]] = float(cells[1]) + float(cells[2])
             except ValueError:
@@ -265,14 +265,20 @@ def _describe_tile(shape):
 
 def _roofline(prof_avg, ms_per_step, ncell, nsrc, n_array, workload, tile_shape):
     peak, peak_src = _peaks()
-    kern = {k: prof_avg.get(k, 0.0) + prof_avg.get(k + "_general", 0.0) for k in ("half", "full")}
-    kern.update({k: prof_avg[k] for k in ("sweep1", "sweep2", "ratedt") if k in prof_avg})
+    # each pass with its helper launches: a trace with the packing of its input
+    # (throughput tiles), the Eq. 4 pass with its verifying re-run, an
+    # integration with its general pass
+    parts = {"half": ["half", "half_general"], "full": ["full", "full_general"],
+             "ratedt": ["ratedt", "ratedt_verify"], "sweep1": ["sweep1", "pack"], "sweep2": ["sweep2", "pack"]}
+    label = {"half": " (closed-form + general pass)", "full": " (closed-form + general pass)",
+             "ratedt": " (pass + verifying pass)", "sweep1": " (n x packing + sweep)", "sweep2": " (n x packing + sweep)"}
+    kern = {k: sum(prof_avg.get(q, 0.0) for q in v) for k, v in parts.items() if v[0] in prof_avg}
     dom = max(kern, key=lambda k: kern[k])
     bpc = kernel_bytes_per_cell(dom, 4, nsrc, n_array)
     achieved = bpc * ncell / (kern[dom] / 1e3) / 1e9
     sbytes = step_bytes_per_cell(nsrc, n_array)
-    kinds = [dom, dom + "_general"] if dom in ("half", "full") else [dom]
-    return {"bound": "hbm", "kernel": dom + (" (closed-form + general pass)" if dom in ("half", "full") else ""),
+    kinds = [q for q in parts[dom] if q in prof_avg]
+    return {"bound": "hbm", "kernel": dom + (label[dom] if len(kinds) > 1 else ""),
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": _traffic(workload, kinds, tile_shape),
             "traffic_unit": "bytes per launch (ncu dram read + write, profiles/)", "peak_source": peak_src,

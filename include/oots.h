@@ -199,6 +199,8 @@ int oots_run_substeps(oots_ctx *ctx, long long n, double t_end);
 #define OOTS_K_FULL_GENERAL 10 /* full step, cells no closed form settles (one warp each) */
 #define OOTS_K_PLANE_TRACE 11  /* columns of the plane-parallel sources (either trace) */
 #define OOTS_K_PLANE_IMPLICIT 12 /* A1 row integration of a plane-parallel source */
+#define OOTS_K_PACK      13  /* n x of the traced state into tile bricks (before each throughput trace) */
+#define OOTS_K_RATEDT_VERIFY 14 /* several sources: re-run of the Eq. 4 pass when the step hint was too short */
 int oots_profile_substep(oots_ctx *ctx, int *kinds, double *ms, int nmax, int *n_out);
 
 /* ---- read-back --------------------------------------------------------------------------- */

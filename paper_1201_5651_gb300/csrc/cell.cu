@@ -631,10 +631,8 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_ker
                         ampsum += __expf(la);
                         SrcRate<Real> t;
                         src_rate<Real>(t, G.qfac[s], G.tab[s], G.sigma0, G.dx, n, G.pcode[s] != 0, i, j, k, N, tabs);
-                        CellODE<Real> C1;
-                        C1.ns = 1; C1.c = c; C1.b0 = Real(0); C1.r = &t; C1.tabs = tabs;
-                        Real Fs, dFs;
-                        ode_F<Real, 1>(C1, x0, &Fs, &dFs);
+                        Real Fs = Real(0), dFs = Real(0);
+                        src_F_term<Real>(t, tabs, x0, Fs, dFs);       // this source's term of F(x0), F'(x0)
                         F += Fs;
                         dF += dFs;
                     }
@@ -922,6 +920,7 @@ cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *
                         Real *qrec, Real *rcache, int use_cache, int gen_blocks, cudaStream_t s)
 {
     if (total <= 0) return cudaSuccess;
+    if (op == OP_RATEDT_VERIFY && nsmax <= 1) return cudaSuccess;     // the single-source pass uses no hint
     if (nsmax <= 1)
         return launch_cell_ns<Real, 1>(grids, ngrid, offsets, total, tabs, op, queue, qcount, qrec, rcache,
                                        use_cache && rcache, gen_blocks, s);
@@ -931,6 +930,8 @@ cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *
     switch (op) {
     case OP_RATEDT:
         cell_multi_kernel<Real, OP_RATEDT><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0);
+        break;
+    case OP_RATEDT_VERIFY:
         // the verifying pass: a few resident blocks that return unless the minimum exceeded the hint
         cell_multi_kernel<Real, OP_RATEDT><<<(unsigned)std::min<long long>(nb, 8LL * gen_blocks), bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 1);
         break;

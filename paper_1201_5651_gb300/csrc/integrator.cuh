@@ -114,26 +114,30 @@ template <typename Real> struct IntResult {
     Real lnfav;  // ln <exp(-b0 x)> over the step
 };
 
+// One source's term of F(x) and F'(x), added to s and d
+template <typename Real>
+OOTS_HD __forceinline__ void src_F_term(const SrcRate<Real> &r, const DevTable<Real> *tabs, Real x, Real &s, Real &d)
+{
+    if (!(r.A > Real(0))) return;
+    if (r.tab < 0) {
+        Real e = m_expm1(-r.b * x);          // e^{-bx} - 1
+        s += -r.A * e;
+        d += r.A * r.b * (Real(1) + e);
+    } else {
+        const DevTable<Real> &T = tabs[r.tab];
+        Real dl = tab_dlnp(T, r.Nin, r.b * x);
+        s += -r.A * r.p * m_expm1(dl);
+        Real px = r.p * m_exp(dl);            // P(Nin + b x)/Q
+        if (px > Real(0)) d += -r.A * px * r.b * tab_dlnp_dN(T, r.Nin + r.b * x);
+    }
+}
+
 // F(x) and F'(x)
 template <typename Real, int NSMAX = MAX_SRC>
 OOTS_HD OOTS_NOINLINE void ode_F(const CellODE<Real> &C, Real x, Real *F, Real *dF)
 {
     Real s = Real(0), d = Real(0);
-    for (int i = 0; i < NSMAX && i < C.ns; i++) {
-        const SrcRate<Real> &r = C.r[i];
-        if (!(r.A > Real(0))) continue;
-        if (r.tab < 0) {
-            Real e = m_expm1(-r.b * x);          // e^{-bx} - 1
-            s += -r.A * e;
-            d += r.A * r.b * (Real(1) + e);
-        } else {
-            const DevTable<Real> &T = C.tabs[r.tab];
-            Real dl = tab_dlnp(T, r.Nin, r.b * x);
-            s += -r.A * r.p * m_expm1(dl);
-            Real px = r.p * m_exp(dl);            // P(Nin + b x)/Q
-            if (px > Real(0)) d += -r.A * px * r.b * tab_dlnp_dN(T, r.Nin + r.b * x);
-        }
-    }
+    for (int i = 0; i < NSMAX && i < C.ns; i++) src_F_term(C.r[i], C.tabs, x, s, d);
     *F = s;
     *dF = d;
 }

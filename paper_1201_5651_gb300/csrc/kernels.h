@@ -78,7 +78,7 @@ cudaError_t launch_plane(const GridDev<Real> *grids, const PlaneJob *jobs, int n
 
 // Per-cell passes.  HALF and FULL run as a closed-form pass over all cells
 // followed by the general pass (op | OP_GENERAL) over the queued cells.
-enum { OP_RATEDT = 0, OP_HALF = 1, OP_FULL1 = 2, OP_FULL2 = 3, OP_GENERAL = 16 };
+enum { OP_RATEDT = 0, OP_HALF = 1, OP_FULL1 = 2, OP_FULL2 = 3, OP_RATEDT_VERIFY = 4, OP_GENERAL = 16 };
 // qrec: per queue slot the closed-form pass's rates and f(x0) of single-source
 // cells (queue_record_bytes each), so the general pass starts at the root
 // search (unused, may be null, when nsmax > 1).  rcache: 3 x total values per

@@ -463,8 +463,11 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
             CU(cudaMemsetAsync(d_sync, 0, 2 * sizeof(unsigned), s));   // ticket and done; the epoch persists
             if (prof) prof->mark(0);
             // the trace's input in bricks (timed with the trace)
-            if (mode == 0 && brick_max > 0)
+            if (mode == 0 && brick_max > 0) {
                 CU(launch_pack_nx<Real>(d_grids, (int)ctxs.size(), which, shape, brick_max, ctxs[0]->nsm, s));
+                if (prof) prof->mark(OOTS_K_PACK);
+                if (prof) prof->mark(0);
+            }
             CU(launch_sweep<Real>(params(which), shape, mode, mode == 0 ? nblocks0 : nblocks1, s));
             if (prof) prof->mark(mode == 1 ? OOTS_K_IMPLICIT : (which == 0 ? OOTS_K_SWEEP1 : OOTS_K_SWEEP2));
         }
@@ -483,7 +486,15 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op, nsmax, d_queue, d_qcount, d_qrec,
                              d_rcache, use_cache ? 1 : 0, gen_blocks, s));
         if (prof) prof->mark(op == OP_RATEDT ? OOTS_K_RATEDT : (op == OP_HALF ? OOTS_K_HALF : OOTS_K_FULL));
-        if (op == OP_RATEDT) return OOTS_OK;
+        if (op == OP_RATEDT) {
+            if (nsmax <= 1) return OOTS_OK;
+            // several sources: the pass that checks the step hint
+            if (prof) prof->mark(0);
+            CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, OP_RATEDT_VERIFY, nsmax, d_queue,
+                                 d_qcount, d_qrec, d_rcache, use_cache ? 1 : 0, gen_blocks, s));
+            if (prof) prof->mark(OOTS_K_RATEDT_VERIFY);
+            return OOTS_OK;
+        }
         // the cells no closed form settles, one warp each
         if (prof) prof->mark(0);
         CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op | OP_GENERAL, nsmax, d_queue,

@@ -43,7 +43,8 @@ EXPORTS = [
 ]
 OOTS_PH_TRACE1, OOTS_PH_DT, OOTS_PH_STEP1, OOTS_PH_TRACE2, OOTS_PH_FULL = 0, 1, 2, 3, 4
 KERNEL_KINDS = {1: "sweep1", 2: "ratedt", 3: "final0", 4: "half", 5: "sweep2", 6: "full", 7: "final1", 8: "implicit",
-                9: "half_general", 10: "full_general", 11: "plane_trace", 12: "plane_implicit"}
+                9: "half_general", 10: "full_general", 11: "plane_trace", 12: "plane_implicit",
+                13: "pack", 14: "ratedt_verify"}
 
 
 class OotsError(RuntimeError):
