@@ -32,6 +32,20 @@ __device__ __forceinline__ int find_grid(const long long *off, int ngrid, long l
     return lo;
 }
 
+// Whether the pass has work on grids lo..hi: the Eq. 4 pass on a grid that
+// has not reached its end time, an integration on a grid with a step in
+// flight.  Blocks of grids past their end return at once, so substeps
+// enqueued beyond the end cost little.
+template <typename Real, int OP>
+__device__ __forceinline__ bool cells_live(const GridDev<Real> *grids, int lo, int hi)
+{
+    for (int q = lo; q <= hi; q++) {
+        const DevState *sq = grids[q].st;
+        if (OP == OP_RATEDT ? !sq->done : sq->dt > 0.0) return true;
+    }
+    return false;
+}
+
 // Rate parameters of every source for the cell at global index g = (X,Y,Z).
 // with_p = false leaves r[s].p of tabulated sources to the caller.
 template <typename Real, int NSMAX>
@@ -99,6 +113,7 @@ __global__ void __launch_bounds__(256, 4) cell_kernel(const GridDev<Real> *grids
         if (last >= total) last = total - 1;
         s_grid_lo = find_grid(offsets, ngrid, base < total ? base : total - 1);
         s_grid_hi = find_grid(offsets, ngrid, last);
+        if (!cells_live<Real, OP>(grids, s_grid_lo, s_grid_hi)) s_grid_hi = s_grid_lo - 1;
     }
     __syncthreads();
     // mixed path: the step and the Eq. 4 factors in FP32, converted once per
@@ -553,6 +568,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_ker
         if (last >= total) last = total - 1;
         s_grid_lo = find_grid(offsets, ngrid, base);
         s_grid_hi = find_grid(offsets, ngrid, last);
+        if (!cells_live<Real, OP>(grids, s_grid_lo, s_grid_hi)) s_grid_hi = s_grid_lo - 1;
     }
     __syncthreads();
     for (int gi = s_grid_lo; gi <= s_grid_hi; gi++) {

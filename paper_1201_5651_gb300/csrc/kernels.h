@@ -47,6 +47,8 @@ template <typename Real> struct SweepParams {
     long long spin_limit;              // bounded wait on upstream tiles
     long long skip_publish;            // tile that never writes its faces (fault-injection test), -1: none
     int chunk;                         // planes per hand-off chunk (<= 0: 4)
+    int ngrid;                         // grids in `grids` (> 0: the launch returns at once when every
+                                       // grid has reached its end time; 0: no such check)
 };
 
 // tagged 8-byte words per published face cell (mixed path 3, FP64 path 4)

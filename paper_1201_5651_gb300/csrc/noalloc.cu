@@ -194,6 +194,7 @@ int trace_noalloc(DevSetup &S, int nx, int ny, int nz, double dx, const void *n_
     P.spin_limit = 1ll << 22;
     P.skip_publish = -1;
     P.chunk = 0;
+    P.ngrid = 0;
     const int prec = sizeof(Real) == 8 ? 0 : 1;
     if (launch_sweep<Real>(P, kShape, 0, S.nblocks[prec], st) != cudaSuccess) return -1;
     return 0;

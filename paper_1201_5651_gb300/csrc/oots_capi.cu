@@ -452,6 +452,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         P.spin_limit = spin_limit;
         P.skip_publish = skip_publish;
         P.chunk = sweep_chunk;
+        P.ngrid = (int)ctxs.size();
         return P;
     }
 

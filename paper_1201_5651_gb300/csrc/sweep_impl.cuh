@@ -266,6 +266,17 @@ constexpr FaceList<TX, TY, TZ> make_face_list()
 template <int TX, int TY, int TZ>
 __device__ const FaceList<TX, TY, TZ> g_face_list = make_face_list<TX, TY, TZ>();
 
+// Whether some grid of the launch has not reached its end time (true when
+// the launch does not say how many grids it holds).  A launch whose grids are
+// all done claims no tile, so substeps past the end cost little.
+template <typename Real> __device__ __forceinline__ bool sweep_live(const SweepParams<Real> &P)
+{
+    if (P.ngrid <= 0) return true;
+    for (int q = 0; q < P.ngrid; q++)
+        if (!P.grids[q].st->done) return true;
+    return false;
+}
+
 template <typename Real, int TX, int TY, int TZ, int MODE>
 __global__ void __launch_bounds__(TY *TZ + 64)
 sweep_kernel(SweepParams<Real> P)
@@ -337,9 +348,10 @@ sweep_kernel(SweepParams<Real> P)
         return la == 0 || ((mode & 4) && l1 == 0) || ((mode & 8) && l2 == 0);
     };
 
+    const bool live = tid == 0 && sweep_live(P);     // read by thread 0 only
     for (;;) {
         if (tid == 0) {
-            unsigned t = atomicAdd(P.ticket, 1u);
+            unsigned t = live ? atomicAdd(P.ticket, 1u) : (unsigned)P.nitems;
             // a grid that has reached its end time skips every tile (all its
             // tiles skip, so no wait is left pending)
             if (t < (unsigned)P.nitems && P.grids[P.jobs[P.items[t].job].grid].st->done) t |= 0x80000000u;

@@ -177,6 +177,7 @@ __global__ void __launch_bounds__(256) pack_nx_kernel(const GridDev<Real> *grids
     Real *B = G.nxb;
     if (B == nullptr) return;
     constexpr unsigned NC = TX * 64u;
+    if (G.st->done) return;                          // past its end time: nothing is traced
     const Real *xs = which == 1 ? G.xh : G.x;
     const Real *n = G.n;
     const Real nu = G.n_uniform;
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? (TX == 8 ? 16 : 9) : 8
         return t;
     };
 
-    if (tid == 0) s_next = claim();
+    if (tid == 0) s_next = sweep_live(P) ? claim() : (unsigned)P.nitems;
     __syncthreads();
     for (;;) {
         const unsigned tk = s_next;
