@@ -251,7 +251,9 @@ __global__ void __launch_bounds__(256, 4) cell_kernel(const GridDev<Real> *grids
             if (threadIdx.x == 0) {
                 double m = sh[0];
                 for (int w = 1; w < (int)(blockDim.x >> 5); w++) m = fmin(m, sh[w]);
-                if (m < 1e300) atomicMin(&st->dt_bits, (unsigned long long)__double_as_longlong(m));
+                // (the read skips the atomic of a block that cannot lower the minimum)
+                const unsigned long long mb = (unsigned long long)__double_as_longlong(m);
+                if (m < 1e300 && mb < *(volatile unsigned long long *)&st->dt_bits) atomicMin(&st->dt_bits, mb);
             }
         } else if (OP == OP_FULL1 || OP == OP_FULL2) {
             double si = ions, sr = rec;
@@ -531,10 +533,12 @@ __device__ __forceinline__ bool closed_form_from_F(Real c, Real x0, Real h, Real
 // (A3's half step, A2's full step), which settles photon-free and slow cells
 // from the cache alone.  A3's full step (new columns) and the cells the cache
 // does not settle select their sources for the step and run the closed forms
-// on them; the rest go to the general pass.  The kernel walks 256-cell
+// on them; the rest go to the general pass.  The kernel walks MULTI_BS-cell
 // chunks with a stride of the grid size.
+constexpr int MULTI_BS = 128;   // threads (and cells) per block of the closed-form passes: small blocks, so that
+                                // the few slow cells of a block hold up few others at its barriers
 template <typename Real, int OP>
-__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_kernel(const GridDev<Real> *grids, int ngrid,
+__global__ void __launch_bounds__(MULTI_BS, sizeof(Real) == 4 ? 8 : 4) cell_multi_kernel(const GridDev<Real> *grids, int ngrid,
                                                          const long long *offsets, long long total,
                                                          const DevTable<Real> *tabs, unsigned *queue,
                                                          unsigned *qcount, Real *rcache, int use_cache, int verify)
@@ -544,7 +548,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_ker
     __shared__ double s_h, s_hint;
     __shared__ float s_lnthr, s_f[4];
     constexpr bool F32 = sizeof(Real) == 4;
-    const long long nchunk = (total + 255) / 256;
+    const long long nchunk = (total + MULTI_BS - 1) / MULTI_BS;
     if (OP == OP_RATEDT && verify) {
         // nothing to do unless some grid's first-pass minimum exceeded its hint
         if (threadIdx.x == 0) {
@@ -562,7 +566,7 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_ker
         if (!s_skip) return;
     }
     for (long long chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
-    const long long base = chunk * 256;
+    const long long base = chunk * MULTI_BS;
     if (threadIdx.x == 0) {
         long long last = base + blockDim.x - 1;
         if (last >= total) last = total - 1;
@@ -594,9 +598,10 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_ker
                     hint = __longlong_as_double(0x7ff0000000000000ll);
                 }
                 s_hint = hint;
-                s_lnthr = lnthr_step<Real>(hint);
+                // the hint's threshold, set with the last step (-inf: no hint, keep every source)
+                s_lnthr = hint < 1e300 ? st->lnthr[0] : -__int_as_float(0x7f800000);
             } else {
-                s_lnthr = lnthr_step<Real>(h);
+                s_lnthr = st->lnthr[OP == OP_HALF ? 1 : 2];
             }
             s_f[0] = float(h);
             s_f[1] = float(st->K1);
@@ -756,7 +761,9 @@ __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2) cell_multi_ker
             if (threadIdx.x == 0) {
                 double mn = sh[0];
                 for (int w = 1; w < (int)(blockDim.x >> 5); w++) mn = fmin(mn, sh[w]);
-                if (mn < 1e300) atomicMin(&st->dt_bits, (unsigned long long)__double_as_longlong(mn));
+                // (the read skips the atomic of a block that cannot lower the minimum)
+                const unsigned long long mb = (unsigned long long)__double_as_longlong(mn);
+                if (mn < 1e300 && mb < *(volatile unsigned long long *)&st->dt_bits) atomicMin(&st->dt_bits, mb);
             }
         } else if (OP == OP_FULL1 || OP == OP_FULL2) {
             double si = ions, sr = rec;
@@ -814,7 +821,7 @@ cell_multi_general_kernel(const GridDev<Real> *grids, int ngrid, const long long
         const Real *Ncol = (OP == OP_FULL2) ? G.N2 : G.N1;
         const double hd = OP == OP_HALF ? 0.5 * dtd : dtd;
         const Real h = Real(hd);
-        const float lnthr = lnthr_step<Real>(hd);
+        const float lnthr = st->lnthr[OP == OP_HALF ? 1 : 2];
         IntResult<Real> R;
         Real F0, dF0, f0;
         SrcRate<Real> r[NACT_GEN];
@@ -875,25 +882,33 @@ __global__ void finalize_kernel(const GridDev<Real> *grids, int ngrid, int stage
     if (gi >= ngrid) return;
     DevState *st = grids[gi].st;
     if (stage == 0) {
-        double dt = 0.0;
+        double dt = 0.0, dcrit = 0.0;
         if (!st->done) {
             if (st->dt_fixed > 0) dt = st->dt_fixed;
             else if (st->dt_bits != 0xffffffffffffffffull) dt = __longlong_as_double((long long)st->dt_bits);
             else dt = st->t_end - st->t;
+            dcrit = dt;
             const double rem = st->t_end - st->t;
             if (dt >= rem * (1.0 - 1e-12)) dt = rem;
             if (!(dt > 0.0)) { dt = 0.0; st->done = 1; }
         }
         st->dt = dt;
-        if (dt > 0.0) st->dt_last = dt;
+        // the hint of the next dt pass: the step the criterion asked for (a
+        // step cut short to land on t_end leaves it as it was asked)
+        if (dt > 0.0) {
+            st->dt_last = dcrit > dt ? dcrit : dt;
+            st->lnthr[0] = lnthr_step<Real>(4.0 * st->dt_last);
+            st->lnthr[1] = lnthr_step<Real>(0.5 * dt);
+            st->lnthr[2] = lnthr_step<Real>(dt);
+        }
         st->dt_bits = 0xffffffffffffffffull;
         const GridDev<Real> &G = grids[gi];
         if (G.nstar && dt > 0.0) {
-            // thresholds of the next dt pass (hint 4 dt), the half step and the full step
+            // thresholds of the next dt pass (its hint, 4 dt_last), the half step and the full step
             for (int s = 0; s < G.nsrc; s++) {
-                G.nstar[s] = negligible_column<Real>(G, tabs, s, lnthr_step<Real>(4.0 * dt));
-                G.nstar[MAX_SRC + s] = negligible_column<Real>(G, tabs, s, lnthr_step<Real>(0.5 * dt));
-                G.nstar[2 * MAX_SRC + s] = negligible_column<Real>(G, tabs, s, lnthr_step<Real>(dt));
+                G.nstar[s] = negligible_column<Real>(G, tabs, s, st->lnthr[0]);
+                G.nstar[MAX_SRC + s] = negligible_column<Real>(G, tabs, s, st->lnthr[1]);
+                G.nstar[2 * MAX_SRC + s] = negligible_column<Real>(G, tabs, s, st->lnthr[2]);
             }
         }
         st->bud_step[0] = st->sumQ * dt;
@@ -940,23 +955,24 @@ cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *
     if (nsmax <= 1)
         return launch_cell_ns<Real, 1>(grids, ngrid, offsets, total, tabs, op, queue, qcount, qrec, rcache,
                                        use_cache && rcache, gen_blocks, s);
-    const int bs = 256;
+    const int bs = MULTI_BS;
     const long long nb = (total + bs - 1) / bs;
     const int uc = use_cache && rcache ? 1 : 0;
+    const int gbs = 256;                 // the general pass's blocks
     switch (op) {
     case OP_RATEDT:
         cell_multi_kernel<Real, OP_RATEDT><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0);
         break;
     case OP_RATEDT_VERIFY:
         // the verifying pass: a few resident blocks that return unless the minimum exceeded the hint
-        cell_multi_kernel<Real, OP_RATEDT><<<(unsigned)std::min<long long>(nb, 8LL * gen_blocks), bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 1);
+        cell_multi_kernel<Real, OP_RATEDT><<<(unsigned)std::min<long long>(nb, 8LL * gen_blocks * (256 / bs)), bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 1);
         break;
     case OP_HALF: cell_multi_kernel<Real, OP_HALF><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0); break;
     case OP_FULL1: cell_multi_kernel<Real, OP_FULL1><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0); break;
     case OP_FULL2: cell_multi_kernel<Real, OP_FULL2><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0); break;
-    case OP_HALF | OP_GENERAL: cell_multi_general_kernel<Real, OP_HALF><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
-    case OP_FULL1 | OP_GENERAL: cell_multi_general_kernel<Real, OP_FULL1><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
-    case OP_FULL2 | OP_GENERAL: cell_multi_general_kernel<Real, OP_FULL2><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
+    case OP_HALF | OP_GENERAL: cell_multi_general_kernel<Real, OP_HALF><<<gen_blocks, gbs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
+    case OP_FULL1 | OP_GENERAL: cell_multi_general_kernel<Real, OP_FULL1><<<gen_blocks, gbs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
+    case OP_FULL2 | OP_GENERAL: cell_multi_general_kernel<Real, OP_FULL2><<<gen_blocks, gbs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -49,6 +49,8 @@ template <typename Real> struct SweepParams {
     int chunk;                         // planes per hand-off chunk (<= 0: 4)
     int ngrid;                         // grids in `grids` (> 0: the launch returns at once when every
                                        // grid has reached its end time; 0: no such check)
+    const void *bricks;                // throughput kernel: base of the packed n x of every grid, brick
+                                       // TileItem::brick at bricks + brick x TX x 64 values (nullptr: none)
 };
 
 // tagged 8-byte words per published face cell (mixed path 3, FP64 path 4)

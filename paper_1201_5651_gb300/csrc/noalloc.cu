@@ -98,6 +98,7 @@ __global__ void build_worklist(const Job *jobs, int njobs, unsigned *count, unsi
             it.J = (unsigned short)Jj;
             it.K = (unsigned short)K;
             it.pad = 0;
+            it.brick = 0u;
             items[pos] = it;
         }
     }
@@ -195,6 +196,7 @@ int trace_noalloc(DevSetup &S, int nx, int ny, int nz, double dx, const void *n_
     P.skip_publish = -1;
     P.chunk = 0;
     P.ngrid = 0;
+    P.bricks = nullptr;
     const int prec = sizeof(Real) == 8 ? 0 : 1;
     if (launch_sweep<Real>(P, kShape, 0, S.nblocks[prec], st) != cudaSuccess) return -1;
     return 0;

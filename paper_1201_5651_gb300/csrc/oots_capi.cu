@@ -154,7 +154,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     unsigned long long *d_faces = nullptr;
     Real *d_tpfaces = nullptr;         // throughput sweep: untagged faces, and a flag per tile
     unsigned *d_tpflags = nullptr;
-    std::vector<void *> brickmem;      // throughput sweep: per grid n x in bricks of the tile
+    Real *d_bricks = nullptr;          // throughput sweep: n x of every grid in bricks of the tile
     long long brick_max = 0;           // brick cells of the largest grid (0: no bricks)
     PlaneJob *d_pjobs = nullptr;       // plane-parallel sources
     int npjobs = 0, nrow0 = 0;         // jobs; of them, rows along x (first in the array)
@@ -192,7 +192,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         cudaFree(d_pjobs);
         cudaFree(d_tabs);
         for (void *p : tabmem) cudaFree(p);
-        for (void *p : brickmem) cudaFree(p);
+        cudaFree(d_bricks);
         cudaFree(d_offsets);
         cudaFree(d_queue);
         cudaFree(d_qrec);
@@ -252,10 +252,22 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         std::vector<DevTable<Real>> tabs;
         std::vector<long long> offs(cs.size());
         long long tile_base = 0, off = 0;
+        // the throughput kernel's traces read n x packed in bricks of the tile
+        // (tiles at global multiples of the tile only), one allocation for all grids
+        const bool pack = is_tp_shape(shape) && scheme != OOTS_A1;
+        std::vector<long long> brick_base(cs.size(), -1);
+        long long nbricks = 0;
         for (size_t g = 0; g < cs.size(); g++) {
             oots_ctx *c = cs[g];
             GridDev<Real> &G = grids[g];
             memset(&G, 0, sizeof(G));
+            if (pack && !c->tile_align) {
+                G.nbx = (c->nx + TX - 1) / TX;
+                G.nby = (c->ny + TY - 1) / TY;
+                G.nbz = (c->nz + TZ - 1) / TZ;
+                brick_base[g] = nbricks;
+                nbricks += (long long)G.nbx * G.nby * G.nbz;
+            }
             G.nx = c->nx; G.ny = c->ny; G.nz = c->nz;
             G.ncell = c->ncell;
             {
@@ -333,6 +345,18 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
                                 t.J = (unsigned short)Jj;
                                 t.K = (unsigned short)K;
                                 t.pad = 0;
+                                t.brick = 0u;
+                                if (brick_base[g] >= 0) {
+                                    // lowest global cell of the tile along each axis (a multiple of the tile)
+                                    const int idx3[3] = {I, Jj, K};
+                                    long long b3[3];
+                                    for (int a = 0; a < 3; a++) {
+                                        const int o0 = idx3[a] * T3[a] - J.off[a];
+                                        const int lo = J.sg[a] > 0 ? J.v[a] + o0 : J.v[a] - o0 - T3[a];
+                                        b3[a] = lo / T3[a];
+                                    }
+                                    t.brick = (unsigned)(brick_base[g] + (b3[2] * G.nby + b3[1]) * G.nbx + b3[0]);
+                                }
                                 items.push_back(t);
                             }
                     tile_base += (long long)J.nt[0] * J.nt[1] * J.nt[2];
@@ -350,22 +374,18 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         });
 
         CU(cudaSetDevice(device));
-        // bricks of n x for the throughput kernel's traces (tiles at global multiples of the tile only)
-        if (is_tp_shape(shape) && scheme != OOTS_A1 && !jobs.empty()) {
+        if (nbricks > 0 && !jobs.empty()) {
+            if (nbricks > 0xffffffffll) return fail(OOTS_E_INVAL, "%lld bricks in one call (32-bit brick indices)", nbricks);
+            const long long bc = (long long)TX * TY * TZ;
+            CU(cudaMalloc(&d_bricks, (size_t)(nbricks * bc) * sizeof(Real)));
             for (size_t g = 0; g < cs.size(); g++) {
-                oots_ctx *c = cs[g];
-                if (c->tile_align) continue;
+                if (brick_base[g] < 0) continue;
                 GridDev<Real> &G = grids[g];
-                G.nbx = (c->nx + TX - 1) / TX;
-                G.nby = (c->ny + TY - 1) / TY;
-                G.nbz = (c->nz + TZ - 1) / TZ;
-                const long long cells = (long long)G.nbx * G.nby * G.nbz * TX * TY * TZ;
-                void *p = nullptr;
-                CU(cudaMalloc(&p, (size_t)cells * sizeof(Real)));
-                brickmem.push_back(p);
-                G.nxb = (Real *)p;
-                brick_max = std::max(brick_max, cells);
+                G.nxb = d_bricks + brick_base[g] * bc;
+                brick_max = std::max(brick_max, (long long)G.nbx * G.nby * G.nbz * bc);
             }
+        } else {
+            for (auto &G : grids) G.nbx = G.nby = G.nbz = 0;
         }
         if (nsmax > 1) {
             // no threshold until the first step sets them (+inf: every source is looked at)
@@ -453,6 +473,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         P.skip_publish = skip_publish;
         P.chunk = sweep_chunk;
         P.ngrid = (int)ctxs.size();
+        P.bricks = d_bricks;
         return P;
     }
 

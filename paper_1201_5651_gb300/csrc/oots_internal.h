@@ -34,8 +34,10 @@ struct PlaneJob {
     long long first;       // first thread of the job in the launch (a multiple of 256)
 };
 
-// One tile of a job, ordered in the work list by tile diagonal I+J+K.
-struct TileItem { int job; unsigned short I, J, K, pad; };
+// One tile of a job, ordered in the work list by tile diagonal I+J+K.  brick:
+// the tile's brick in the launch's packed n x (GridDev::nxb counts from the
+// same base), when the launch packs its input (throughput tiles).
+struct TileItem { int job; unsigned short I, J, K, pad; unsigned brick; };
 
 // Per-grid state that lives on the device, read and written by the kernels
 // (so that substeps can be replayed from a CUDA graph without host sync).
@@ -53,7 +55,9 @@ struct DevState {
     long long nsub;           // substeps taken
     int done;                 // t >= t_end
     int err;                  // DEVERR_*
-    int pad[2];
+    float lnthr[4];           // source-selection thresholds ln(1e-3 eps / H), set with each step: the next
+                              // dt pass's (H = 4 dt_last; used while dt_last > 0), the half step's
+                              // (H = dt/2) and the full step's (H = dt); [3] unused
 };
 
 // Description of one grid for the kernels (Real = float or double).

@@ -135,6 +135,11 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+// Start fetching `bytes` (a multiple of 16, 16-byte aligned) into L2, without waiting.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // Reciprocal and square root: correctly rounded in FP64, the fast
 // approximations in the mixed path (a few ulp; the mixed path is judged on its
@@ -234,27 +239,21 @@ __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? (TX == 8 ? 16 : 9) : 8
     const int tid = threadIdx.x;
     const int c8 = tid % 8, r8 = tid / 8;             // (j,k) column of this thread
 
-    // a ticket, marked when its grid has already reached its end time
-    auto claim = [&]() {
-        unsigned t = atomicAdd(P.ticket, 1u);
-        if (t < (unsigned)P.nitems && P.grids[P.jobs[P.items[t].job].grid].st->done) t |= 0x80000000u;
-        return t;
-    };
-
-    if (tid == 0) s_next = sweep_live(P) ? claim() : (unsigned)P.nitems;
+    if (tid == 0) s_next = sweep_live(P) ? atomicAdd(P.ticket, 1u) : (unsigned)P.nitems;
     __syncthreads();
     for (;;) {
         const unsigned tk = s_next;
-        if ((tk & 0x7fffffffu) >= (unsigned)P.nitems) break;
-        if (tk & 0x80000000u) {
-            __syncthreads();
-            if (tid == 0) s_next = claim();
-            __syncthreads();
-            continue;
-        }
+        if (tk >= (unsigned)P.nitems) break;
         const TileItem it = P.items[tk];
         const Job J = P.jobs[it.job];
         const GridDev<Real> &G = P.grids[J.grid];
+        if (G.st->done) {
+            // a grid past its end time skips every tile (all of them, so no wait is left pending)
+            __syncthreads();
+            if (tid == 0) s_next = atomicAdd(P.ticket, 1u);
+            __syncthreads();
+            continue;
+        }
         const int o0[3] = {it.I * TX - J.off[0], it.J * 8 - J.off[1], it.K * 8 - J.off[2]};
         const long long tile_self = J.tile_base + ((long long)it.K * J.nt[1] + it.J) * J.nt[0] + it.I;
         const Real *xin = (P.which == 1) ? G.xh : G.x;
@@ -278,6 +277,9 @@ __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? (TX == 8 ? 16 : 9) : 8
                 if (ns < 256) ns <<= 1;
             }
         }
+        // the next ticket, claimed now so that it is back by the halo step
+        unsigned tk_next = 0u;
+        if (tid == 0) tk_next = atomicAdd(P.ticket, 1u);
         // 2. own cells: increments n x ds and weight factors.  Cell e = tid + 64 u
         //    (x fastest); the global index moves by fixed strides (octant signs
         //    folded in), four cells' loads in flight at a time.
@@ -289,13 +291,9 @@ __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? (TX == 8 ? 16 : 9) : 8
         const int j_lo = max(-o0[1], 0), j_hi = min(J.ext[1] - o0[1], 8);
         const int k_lo = max(-o0[2], 0), k_hi = min(J.ext[2] - o0[2], 8);
         if (G.nxb != nullptr) {
-            // the tile's brick: its lowest global cell along each axis is a
-            // multiple of the tile; thread tid takes brick cells 4 (tid + 64 v) ..+3
-            const int lo0 = J.sg[0] > 0 ? J.v[0] + o0[0] : J.v[0] - o0[0] - TX;
-            const int lo1 = J.sg[1] > 0 ? J.v[1] + o0[1] : J.v[1] - o0[1] - 8;
-            const int lo2 = J.sg[2] > 0 ? J.v[2] + o0[2] : J.v[2] - o0[2] - 8;
-            const Real *brick =
-                G.nxb + ((long long)((lo2 / 8) * G.nby + lo1 / 8) * G.nbx + lo0 / TX) * (long long)L::NC;
+            // the tile's brick (its index set with the work list); thread tid
+            // takes brick cells 4 (tid + 64 v) .. +3
+            const Real *brick = reinterpret_cast<const Real *>(P.bricks) + (long long)it.brick * L::NC;
 #pragma unroll
             for (int v = 0; v < L::NC / 256; v++) {
                 const int e0 = 4 * (tid + 64 * v);
@@ -377,8 +375,14 @@ __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? (TX == 8 ? 16 : 9) : 8
             sN[h] = vN;
             sW[h] = vW;
         }
-        // claim the next tile while this one sweeps
-        if (tid == 0) s_next = claim();
+        // hand on the next ticket, and start its brick on its way into L2
+        if (tid == 0) {
+            s_next = tk_next;
+            if (P.bricks != nullptr && tk_next < (unsigned)P.nitems)
+                prefetch_l2_bulk(reinterpret_cast<const Real *>(P.bricks) +
+                                     (long long)__ldg(&P.items[tk_next].brick) * L::NC,
+                                 (unsigned)(L::NC * sizeof(Real)));
+        }
         __syncthreads();
 
         // 4. one dominant axis over the whole tile (in-octant cells), or mixed
