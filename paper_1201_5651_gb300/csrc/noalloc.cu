@@ -97,7 +97,7 @@ __global__ void build_worklist(const Job *jobs, int njobs, unsigned *count, unsi
             it.I = (unsigned short)I;
             it.J = (unsigned short)Jj;
             it.K = (unsigned short)K;
-            it.pad = 0;
+            it.grid = 0;
             it.brick = 0u;
             items[pos] = it;
         }

@@ -231,6 +231,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     int build(const std::vector<oots_ctx *> &cs, int shape_req)
     {
         ctxs = cs;
+        if (cs.size() > 65535) return fail(OOTS_E_INVAL, "%zu grids in one call (at most 65535)", cs.size());
         oots_ctx *c0 = cs[0];
         device = c0->device;
         scheme = c0->scheme;
@@ -344,7 +345,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
                                 t.I = (unsigned short)I;
                                 t.J = (unsigned short)Jj;
                                 t.K = (unsigned short)K;
-                                t.pad = 0;
+                                t.grid = (unsigned short)g;
                                 t.brick = 0u;
                                 if (brick_base[g] >= 0) {
                                     // lowest global cell of the tile along each axis (a multiple of the tile)

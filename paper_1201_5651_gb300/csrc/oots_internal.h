@@ -34,10 +34,11 @@ struct PlaneJob {
     long long first;       // first thread of the job in the launch (a multiple of 256)
 };
 
-// One tile of a job, ordered in the work list by tile diagonal I+J+K.  brick:
-// the tile's brick in the launch's packed n x (GridDev::nxb counts from the
-// same base), when the launch packs its input (throughput tiles).
-struct TileItem { int job; unsigned short I, J, K, pad; unsigned brick; };
+// One tile of a job, ordered in the work list by tile diagonal I+J+K.  grid:
+// the job's grid (as Job::grid; launches of at most 65535 grids).  brick: the
+// tile's brick in the launch's packed n x (GridDev::nxb counts from the same
+// base), when the launch packs its input (throughput tiles).
+struct TileItem { int job; unsigned short I, J, K, grid; unsigned brick; };
 
 // Per-grid state that lives on the device, read and written by the kernels
 // (so that substeps can be replayed from a CUDA graph without host sync).

@@ -245,15 +245,16 @@ __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? (TX == 8 ? 16 : 9) : 8
         const unsigned tk = s_next;
         if (tk >= (unsigned)P.nitems) break;
         const TileItem it = P.items[tk];
-        const Job J = P.jobs[it.job];
-        const GridDev<Real> &G = P.grids[J.grid];
-        if (G.st->done) {
-            // a grid past its end time skips every tile (all of them, so no wait is left pending)
+        if (P.ngrid > 1 && P.grids[it.grid].st->done) {
+            // a grid past its end time skips every tile (all of them, so no wait is left pending);
+            // with one grid the launch returned at once instead
             __syncthreads();
             if (tid == 0) s_next = atomicAdd(P.ticket, 1u);
             __syncthreads();
             continue;
         }
+        const Job J = P.jobs[it.job];
+        const GridDev<Real> &G = P.grids[J.grid];
         const int o0[3] = {it.I * TX - J.off[0], it.J * 8 - J.off[1], it.K * 8 - J.off[2]};
         const long long tile_self = J.tile_base + ((long long)it.K * J.nt[1] + it.J) * J.nt[0] + it.I;
         const Real *xin = (P.which == 1) ? G.xh : G.x;
