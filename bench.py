@@ -255,12 +255,17 @@ def step_bytes_per_cell(nsrc, n_array):
     return 28 * nsrc + 32
 
 
-def _describe_tile(shape):
+def _describe_tile(shape, cell_block=None, nsrc=1):
+    """The sweep's tile shape and kernel, and (when given) the threads per block of
+    the closed-form per-cell passes (0 = the library's default for the source count)."""
     from paper_1201_5651_gb300 import oots
     if shape is None:
         return None
     dims = oots.oots_tile_shape_info(shape)[1]
-    return {"id": shape, "dims": list(dims), "kernel": "throughput" if shape in (7, 8) else "pipelined"}
+    d = {"id": shape, "dims": list(dims), "kernel": "throughput" if shape in (7, 8) else "pipelined"}
+    if cell_block is not None:
+        d["cell_block"] = cell_block if cell_block else (128 if nsrc > 1 else 256)
+    return d
 
 
 def _roofline(prof_avg, ms_per_step, ncell, nsrc, n_array, workload, tile_shape):
@@ -343,12 +348,14 @@ def _tuned_context(w, precision, dev, stream, args, devname):
             shape = args.shape
         except oots.OotsError:
             shape = None
+    cb = 0
     if shape is None:
         shape = autotune.tune(c, devname, len(w.sources), use_cache=not args.retune)
+        cb = autotune.lookup_cell_block(devname, c.precision, autotune.plane_class(w.nx, w.ny, w.nz, len(w.sources)))
     c.set_neutral_fraction(w.x0)
     c.set_time(0.0)
     c.reset_budget()
-    return c, shape
+    return c, shape, cb
 
 
 def bench_single(args, name, steps, warmup, rank, world, dev, flush, devname, with_fp64=True):
@@ -359,7 +366,7 @@ def bench_single(args, name, steps, warmup, rank, world, dev, flush, devname, wi
     trec = w.t_rec
     t_end = T_END_RUN * trec
     s = torch.cuda.Stream(device=dev)
-    cm, shape = _tuned_context(w, "mixed", dev, s, args, devname)
+    cm, shape, cblock = _tuned_context(w, "mixed", dev, s, args, devname)
     t_dev0 = time.perf_counter()
     _, ndev = cm.advance(spec["t0"] * trec)            # untimed: develop the fronts
     t_dev = time.perf_counter() - t_dev0
@@ -378,7 +385,7 @@ def bench_single(args, name, steps, warmup, rank, world, dev, flush, devname, wi
     out = {"workload": name, "describe": spec["describe"], "ncell": w.ncell, "nsrc": nsrc,
            "value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
            "t0_over_trec": t0 / trec, "develop_substeps": ndev, "develop_s": t_dev,
-           "tile_shape": _describe_tile(shape),
+           "tile_shape": _describe_tile(shape, cblock, len(w.sources)),
            "roofline": _roofline(prof_avg, ms / steps, w.ncell, nsrc, w.uniform_n is None, name, shape),
            "kernel_ms": prof_avg, "launches_per_substep": launches,
            "cell_sweeps_per_s": 2.0 * value}
@@ -450,6 +457,9 @@ def bench_batch(args, steps, warmup, rank, world, dev, flush, devname):
         c.set_stream(s.cuda_stream)
         ctxs.append(c)
     shape = args.shape if args.shape >= 0 else autotune.tune_batch(ctxs, ws, devname, use_cache=not args.retune)
+    nside = max(max(w.nx, w.ny, w.nz) for w in ws)
+    cblock = 0 if args.shape >= 0 else autotune.lookup_cell_block(
+        devname, oots.OOTS_MIXED, autotune.plane_class(nside, nside, nside, max(len(w.sources) for w in ws), len(ws)))
     for c, w in zip(ctxs, ws):
         if shape is not None:
             c.set_tile_shape(shape)
@@ -467,7 +477,7 @@ def bench_batch(args, steps, warmup, rank, world, dev, flush, devname):
     out = {"workload": "batch64", "describe": spec["describe"], "ngrids": len(ws), "ncell": ncell,
            "value": value, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps, "warmup": warmup,
            "develop_substeps": {"min": int(min(nsub)), "max": int(max(nsub))}, "develop_s": t_dev,
-           "tile_shape": _describe_tile(shape),
+           "tile_shape": _describe_tile(shape, cblock, max(len(w.sources) for w in ws)),
            "roofline": {"bound": "hbm", "kernel": "whole substep (all kernels, one launch each for the 64 grids)",
                         "achieved": sbytes * ncell / (ms / steps / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": sbytes * ncell / (ms / steps / 1e3) / 1e9 / peak, "traffic": None,

@@ -316,8 +316,10 @@ int oots_tile_shape_info(int shape, int dims[3]);
  * default of 4); key 4 = where the sweep's tiles start: 0 (default) at
  * multiples of the tile size in global coordinates (rows of x aligned to
  * memory), 1 at the octant's origin (the octant's diagonal planes then cut
- * only the tiles on the tile diagonals).  OOTS_E_INVAL for an unknown key or
- * a value out of range. */
+ * only the tiles on the tile diagonals); key 5 = threads per block of the
+ * closed-form per-cell passes (the dt criterion, the half and full steps):
+ * 128, 256, or 0 for the default (128 with several sources per grid, 256
+ * with one).  OOTS_E_INVAL for an unknown key or a value out of range. */
 int oots_debug_set(oots_ctx *ctx, int key, long long value);
 
 /* ---- allocation-free trace --------------------------------------------------------------- */

@@ -1,4 +1,5 @@
-"""Autotuner for the wavefront sweep: tile shape and sweep kernel.
+"""Autotuner for a substep's launch shapes: the sweep's tile shape and kernel,
+and the block size of the closed-form per-cell passes.
 
 The sweep has two kernels (the pipelined one, whose tiles hand their faces on
 plane chunk by chunk, and the throughput one, which traces whole 8^3 tiles)
@@ -12,7 +13,11 @@ power of two), the number of sources per grid and the number of grids, each
 bucketed -- rather than on the exact grid, times every shape the device can
 run on one substep (per-launch CUDA events through oots_profile_substep, or
 whole batched substeps), and caches the fastest as JSON keyed by device name,
-precision and class.
+precision and class.  On the chosen shape it then times the closed-form
+per-cell passes (the dt criterion, the half and the full step) with 128- and
+256-thread blocks: small blocks hold up fewer cells behind a slow one at their
+barriers, large ones set up fewer blocks, and which wins depends on how
+uneven the per-cell work is (many sources, fronts).
 """
 from __future__ import annotations
 
@@ -71,6 +76,33 @@ def lookup(device_name: str, precision: int, klass: str, path: str = CACHE) -> O
     return None if e is None else int(e["shape"])
 
 
+def lookup_cell_block(device_name: str, precision: int, klass: str, path: str = CACHE) -> int:
+    """The tuned block size of the closed-form passes (0: none tuned, the library's default)."""
+    e = _load_cache(path).get(cache_key(device_name, precision, klass))
+    return 0 if e is None else int(e.get("cell_block", 0))
+
+
+CELL_KINDS = ("ratedt", "ratedt_verify", "half", "full")
+CELL_BLOCKS = (128, 256)
+
+
+def _tune_cell_block(ctx: "oots.Context", repeats: int) -> Dict[int, float]:
+    """Closed-form pass time of one substep per block size (ms)."""
+    times = {}
+    for bs in CELL_BLOCKS:
+        try:
+            ctx.set_cell_block(bs)
+            ctx.profile_substep()
+            best = None
+            for _ in range(repeats):
+                t = sum(ms for k, ms in ctx.profile_substep() if k in CELL_KINDS)
+                best = t if best is None else min(best, t)
+            times[bs] = best
+        except oots.OotsError:
+            continue
+    return times
+
+
 def _shapes():
     n, _ = oots.oots_tile_shape_info(0)
     return range(n)
@@ -87,6 +119,9 @@ def tune(ctx: "oots.Context", device_name: str, nsrc: int, repeats: int = 2, use
         hit = lookup(device_name, ctx.precision, klass, path)
         if hit is not None:
             ctx.set_tile_shape(hit)
+            cb = lookup_cell_block(device_name, ctx.precision, klass, path)
+            if cb:
+                ctx.set_cell_block(cb)
             return hit
     times = {}
     for sh in _shapes():
@@ -107,17 +142,23 @@ def tune(ctx: "oots.Context", device_name: str, nsrc: int, repeats: int = 2, use
         return None
     choice = min(times, key=times.get)
     ctx.set_tile_shape(choice)
+    ctimes = _tune_cell_block(ctx, repeats)
+    cb = min(ctimes, key=ctimes.get) if ctimes else 0
+    ctx.set_cell_block(cb)
     if verbose:
-        print({sh: round(v, 4) for sh, v in times.items()})
+        print({sh: round(v, 4) for sh, v in times.items()}, {b: round(v, 4) for b, v in ctimes.items()})
     _store(key, {"shape": choice, "dims": oots.oots_tile_shape_info(choice)[1], "class": klass,
-                 "sweep_ms": {str(k): v for k, v in times.items()}}, path)
+                 "sweep_ms": {str(k): v for k, v in times.items()}, "cell_block": cb,
+                 "cell_ms": {str(k): v for k, v in ctimes.items()}}, path)
     return choice
 
 
 def tune_batch(ctxs: Sequence["oots.Context"], workloads, device_name: str, repeats: int = 2,
                use_cache: bool = True, path: str = CACHE) -> Optional[int]:
-    """Time whole batched substeps of the contexts for every tile shape and keep
-    the fastest.  The contexts' states and times are restored afterwards."""
+    """Time whole batched substeps of the contexts for every tile shape, then
+    for each block size of the closed-form passes on the fastest shape; keep
+    the fastest of each (the block size is set on the contexts, the shape
+    returned).  The contexts' states and times are restored afterwards."""
     nside = max(max(w.nx, w.ny, w.nz) for w in workloads)
     nsrc = max(len(w.sources) for w in workloads)
     klass = plane_class(nside, nside, nside, nsrc, len(ctxs))
@@ -126,16 +167,18 @@ def tune_batch(ctxs: Sequence["oots.Context"], workloads, device_name: str, repe
     if use_cache:
         hit = lookup(device_name, prec, klass, path)
         if hit is not None:
+            cb = lookup_cell_block(device_name, prec, klass, path)
+            if cb:
+                for c in ctxs:
+                    c.set_cell_block(cb)
             return hit
     t_end = [10.0 * w.t_rec for w in workloads]
-    times = {}
-    for sh in _shapes():
-        try:
-            for c in ctxs:
-                c.set_tile_shape(sh)
-            b = oots.Batch(ctxs)
-        except oots.OotsError:
-            continue
+
+    def timed(sh, cb):
+        for c in ctxs:
+            c.set_tile_shape(sh)
+            c.set_cell_block(cb)
+        b = oots.Batch(ctxs)
         try:
             b.run_substeps(1, t_end)
             ctxs[0].synchronize()
@@ -146,18 +189,32 @@ def tune_batch(ctxs: Sequence["oots.Context"], workloads, device_name: str, repe
                 ctxs[0].synchronize()
                 dt = time.perf_counter() - t0
                 best = dt if best is None else min(best, dt)
-            times[sh] = best * 1e3
-        except oots.OotsError:
-            pass
+            return best * 1e3
         finally:
             b.close()
+
+    times, ctimes = {}, {}
+    for sh in _shapes():
+        try:
+            times[sh] = timed(sh, 0)
+        except oots.OotsError:
+            continue
+    choice = min(times, key=times.get) if times else None
+    if choice is not None:
+        for cb in CELL_BLOCKS:
+            try:
+                ctimes[cb] = timed(choice, cb)
+            except oots.OotsError:
+                continue
+    cb = min(ctimes, key=ctimes.get) if ctimes else 0
     for c, w in zip(ctxs, workloads):
+        c.set_cell_block(cb)
         c.set_neutral_fraction(w.x0)
         c.set_time(0.0)
         c.reset_budget()
-    if not times:
+    if choice is None:
         return None
-    choice = min(times, key=times.get)
     _store(key, {"shape": choice, "dims": oots.oots_tile_shape_info(choice)[1], "class": klass,
-                 "substep_ms": {str(k): v for k, v in times.items()}}, path)
+                 "substep_ms": {str(k): v for k, v in times.items()}, "cell_block": cb,
+                 "cell_substep_ms": {str(k): v for k, v in ctimes.items()}}, path)
     return choice

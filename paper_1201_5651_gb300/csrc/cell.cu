@@ -98,8 +98,8 @@ __device__ __forceinline__ void block_sum2(double &a, double &b, double *sh)
     }
 }
 
-template <typename Real, int OP, int NSMAX>
-__global__ void __launch_bounds__(256, 4) cell_kernel(const GridDev<Real> *grids, int ngrid, const long long *offsets,
+template <typename Real, int OP, int NSMAX, int BS>
+__global__ void __launch_bounds__(BS, 1024 / BS) cell_kernel(const GridDev<Real> *grids, int ngrid, const long long *offsets,
                                                    long long total, const DevTable<Real> *tabs, unsigned *queue,
                                                    unsigned *qcount, Real *qrec, Real *rcache, int use_cache)
 {
@@ -379,7 +379,6 @@ cell_general_kernel(const GridDev<Real> *grids, int ngrid, const long long *offs
 // float, from the table node at or below the column (P falls as N grows); the
 // rates of the sources kept are then formed exactly, in a few registers.
 constexpr int NACT = 4;        // sources the closed-form passes hold in registers
-constexpr int NACT_GEN = 8;    // sources the general pass holds in registers
 
 // ln P(N)/Q rounded up: the node value one interval below N's
 template <typename Real>
@@ -471,9 +470,13 @@ __device__ __forceinline__ int gather_rates(const GridDev<Real> &G, const Real *
             if (cnt == NK) return NK + 1;
             SrcRate<Real> t;
             src_rate<Real>(t, G.qfac[s], G.tab[s], G.sigma0, G.dx, n, G.pcode[s] != 0, i, j, k, N, tabs);
+            if constexpr (NK <= 16) {
 #pragma unroll
-            for (int u = 0; u < NK; u++)
-                if (u == cnt) r[u] = t;
+                for (int u = 0; u < NK; u++)
+                    if (u == cnt) r[u] = t;
+            } else {
+                r[cnt] = t;                 // a local-memory array: index it directly
+            }
             cnt++;
         }
     }
@@ -533,12 +536,12 @@ __device__ __forceinline__ bool closed_form_from_F(Real c, Real x0, Real h, Real
 // (A3's half step, A2's full step), which settles photon-free and slow cells
 // from the cache alone.  A3's full step (new columns) and the cells the cache
 // does not settle select their sources for the step and run the closed forms
-// on them; the rest go to the general pass.  The kernel walks MULTI_BS-cell
+// on them; the rest go to the general pass.  The kernel walks BS-cell
 // chunks with a stride of the grid size.
-constexpr int MULTI_BS = 128;   // threads (and cells) per block of the closed-form passes: small blocks, so that
-                                // the few slow cells of a block hold up few others at its barriers
-template <typename Real, int OP>
-__global__ void __launch_bounds__(MULTI_BS, sizeof(Real) == 4 ? 8 : 4) cell_multi_kernel(const GridDev<Real> *grids, int ngrid,
+// BS: threads (and cells) per block, 128 or 256 (tuned): small blocks hold up
+// fewer cells at their barriers behind a slow one.
+template <typename Real, int OP, int BS>
+__global__ void __launch_bounds__(BS, (sizeof(Real) == 4 ? 1024 : 512) / BS) cell_multi_kernel(const GridDev<Real> *grids, int ngrid,
                                                          const long long *offsets, long long total,
                                                          const DevTable<Real> *tabs, unsigned *queue,
                                                          unsigned *qcount, Real *rcache, int use_cache, int verify)
@@ -548,7 +551,7 @@ __global__ void __launch_bounds__(MULTI_BS, sizeof(Real) == 4 ? 8 : 4) cell_mult
     __shared__ double s_h, s_hint;
     __shared__ float s_lnthr, s_f[4];
     constexpr bool F32 = sizeof(Real) == 4;
-    const long long nchunk = (total + MULTI_BS - 1) / MULTI_BS;
+    const long long nchunk = (total + BS - 1) / BS;
     if (OP == OP_RATEDT && verify) {
         // nothing to do unless some grid's first-pass minimum exceeded its hint
         if (threadIdx.x == 0) {
@@ -566,7 +569,7 @@ __global__ void __launch_bounds__(MULTI_BS, sizeof(Real) == 4 ? 8 : 4) cell_mult
         if (!s_skip) return;
     }
     for (long long chunk = blockIdx.x; chunk < nchunk; chunk += gridDim.x) {
-    const long long base = chunk * MULTI_BS;
+    const long long base = chunk * BS;
     if (threadIdx.x == 0) {
         long long last = base + blockDim.x - 1;
         if (last >= total) last = total - 1;
@@ -782,9 +785,7 @@ __global__ void __launch_bounds__(MULTI_BS, sizeof(Real) == 4 ? 8 : 4) cell_mult
 }
 
 // General pass of grids with several sources: one lane group per queued
-// cell, as cell_general_kernel, with the sources selected for the step in
-// registers (all of them, in local memory, for the rare cell that more than
-// NACT_GEN sources light).
+// cell, as cell_general_kernel, with the sources selected for the step.
 template <typename Real, int OP>
 __global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2)
 cell_multi_general_kernel(const GridDev<Real> *grids, int ngrid, const long long *offsets, const DevTable<Real> *tabs,
@@ -824,22 +825,16 @@ cell_multi_general_kernel(const GridDev<Real> *grids, int ngrid, const long long
         const float lnthr = st->lnthr[OP == OP_HALF ? 1 : 2];
         IntResult<Real> R;
         Real F0, dF0, f0;
-        SrcRate<Real> r[NACT_GEN];
+        // the sources selected for the step (as the closed-form pass selected them),
+        // in local memory; one instantiation of the integrator keeps the kernel's
+        // code small (its lanes run apart through the root search and quadrature)
+        SrcRate<Real> ra[MAX_SRC];
         const Real *nst = G.nstar ? G.nstar + (OP == OP_HALF ? 1 : 2) * MAX_SRC : nullptr;
-        const int na = gather_rates<Real, NACT_GEN>(G, Ncol, tabs, X, Y, Z, g, n, lnthr, r, nst);
-        if (na <= NACT_GEN) {
-            CellODE<Real> C;
-            C.ns = na; C.c = G.alpha * n; C.b0 = Real(0); C.r = r; C.tabs = tabs;
-            if (!integrate_prelude<Real, NACT_GEN>(C, x0, h, G.sigma0, R, F0, dF0, f0))
-                R = integrate_general<Real, NACT_GEN>(C, x0, h, G.sigma0, R, F0, dF0, f0, GroupEval<W>{lane, gbase, gmask});
-        } else {
-            SrcRate<Real> ra[MAX_SRC];
-            CellODE<Real> C;
-            C.ns = cell_rates<Real, MAX_SRC>(G, Ncol, tabs, X, Y, Z, g, n, ra);
-            C.c = G.alpha * n; C.b0 = Real(0); C.r = ra; C.tabs = tabs;
-            if (!integrate_prelude<Real, MAX_SRC>(C, x0, h, G.sigma0, R, F0, dF0, f0))
-                R = integrate_general<Real, MAX_SRC>(C, x0, h, G.sigma0, R, F0, dF0, f0, GroupEval<W>{lane, gbase, gmask});
-        }
+        CellODE<Real> C;
+        C.ns = gather_rates<Real, MAX_SRC>(G, Ncol, tabs, X, Y, Z, g, n, lnthr, ra, nst);
+        C.c = G.alpha * n; C.b0 = Real(0); C.r = ra; C.tabs = tabs;
+        if (!integrate_prelude<Real, MAX_SRC>(C, x0, h, G.sigma0, R, F0, dF0, f0))
+            R = integrate_general<Real, MAX_SRC>(C, x0, h, G.sigma0, R, F0, dF0, f0, GroupEval<W>{lane, gbase, gmask});
         if (lane == 0) {
             if (OP == OP_HALF) {
                 const_cast<Real *>(G.xh)[g] = R.x;
@@ -923,59 +918,70 @@ __global__ void finalize_kernel(const GridDev<Real> *grids, int ngrid, int stage
     }
 }
 
-template <typename Real, int NSMAX>
+template <typename Real, int NSMAX, int BS>
 static cudaError_t launch_cell_ns(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
                                   const DevTable<Real> *tabs, int op, unsigned *queue, unsigned *qcount,
                                   Real *qrec, Real *rcache, int use_cache, int gen_blocks, cudaStream_t s)
 {
-    const int bs = 256;
-    const long long nb = (total + bs - 1) / bs;
+    const long long nb = (total + BS - 1) / BS;
+    const int gbs = 256;                 // the general pass's blocks
     switch (op) {
-    case OP_RATEDT: cell_kernel<Real, OP_RATEDT, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec, rcache, use_cache); break;
-    case OP_HALF: cell_kernel<Real, OP_HALF, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec, rcache, use_cache); break;
-    case OP_FULL1: cell_kernel<Real, OP_FULL1, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec, rcache, use_cache); break;
-    case OP_FULL2: cell_kernel<Real, OP_FULL2, NSMAX><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec, rcache, use_cache); break;
-    case OP_HALF | OP_GENERAL: cell_general_kernel<Real, OP_HALF, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount, qrec); break;
-    case OP_FULL1 | OP_GENERAL: cell_general_kernel<Real, OP_FULL1, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount, qrec); break;
-    case OP_FULL2 | OP_GENERAL: cell_general_kernel<Real, OP_FULL2, NSMAX><<<gen_blocks, bs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount, qrec); break;
+    case OP_RATEDT: cell_kernel<Real, OP_RATEDT, NSMAX, BS><<<(unsigned)nb, BS, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec, rcache, use_cache); break;
+    case OP_HALF: cell_kernel<Real, OP_HALF, NSMAX, BS><<<(unsigned)nb, BS, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec, rcache, use_cache); break;
+    case OP_FULL1: cell_kernel<Real, OP_FULL1, NSMAX, BS><<<(unsigned)nb, BS, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec, rcache, use_cache); break;
+    case OP_FULL2: cell_kernel<Real, OP_FULL2, NSMAX, BS><<<(unsigned)nb, BS, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, qrec, rcache, use_cache); break;
+    case OP_HALF | OP_GENERAL: cell_general_kernel<Real, OP_HALF, NSMAX><<<gen_blocks, gbs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount, qrec); break;
+    case OP_FULL1 | OP_GENERAL: cell_general_kernel<Real, OP_FULL1, NSMAX><<<gen_blocks, gbs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount, qrec); break;
+    case OP_FULL2 | OP_GENERAL: cell_general_kernel<Real, OP_FULL2, NSMAX><<<gen_blocks, gbs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount, qrec); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-// nsmax: the largest source count of the grids in the call (1 selects the
-// single-source kernels, whose per-source state stays in registers)
-template <typename Real>
-cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
-                        const DevTable<Real> *tabs, int op, int nsmax, unsigned *queue, unsigned *qcount,
-                        Real *qrec, Real *rcache, int use_cache, int gen_blocks, cudaStream_t s)
+template <typename Real, int BS>
+static cudaError_t launch_cell_multi(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
+                                     const DevTable<Real> *tabs, int op, unsigned *queue, unsigned *qcount,
+                                     Real *rcache, int uc, int gen_blocks, cudaStream_t s)
 {
-    if (total <= 0) return cudaSuccess;
-    if (op == OP_RATEDT_VERIFY && nsmax <= 1) return cudaSuccess;     // the single-source pass uses no hint
-    if (nsmax <= 1)
-        return launch_cell_ns<Real, 1>(grids, ngrid, offsets, total, tabs, op, queue, qcount, qrec, rcache,
-                                       use_cache && rcache, gen_blocks, s);
-    const int bs = MULTI_BS;
-    const long long nb = (total + bs - 1) / bs;
-    const int uc = use_cache && rcache ? 1 : 0;
+    const long long nb = (total + BS - 1) / BS;
     const int gbs = 256;                 // the general pass's blocks
     switch (op) {
     case OP_RATEDT:
-        cell_multi_kernel<Real, OP_RATEDT><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0);
+        cell_multi_kernel<Real, OP_RATEDT, BS><<<(unsigned)nb, BS, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0);
         break;
     case OP_RATEDT_VERIFY:
         // the verifying pass: a few resident blocks that return unless the minimum exceeded the hint
-        cell_multi_kernel<Real, OP_RATEDT><<<(unsigned)std::min<long long>(nb, 8LL * gen_blocks * (256 / bs)), bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 1);
+        cell_multi_kernel<Real, OP_RATEDT, BS><<<(unsigned)std::min<long long>(nb, 8LL * gen_blocks * (256 / BS)), BS, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 1);
         break;
-    case OP_HALF: cell_multi_kernel<Real, OP_HALF><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0); break;
-    case OP_FULL1: cell_multi_kernel<Real, OP_FULL1><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0); break;
-    case OP_FULL2: cell_multi_kernel<Real, OP_FULL2><<<(unsigned)nb, bs, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0); break;
+    case OP_HALF: cell_multi_kernel<Real, OP_HALF, BS><<<(unsigned)nb, BS, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0); break;
+    case OP_FULL1: cell_multi_kernel<Real, OP_FULL1, BS><<<(unsigned)nb, BS, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0); break;
+    case OP_FULL2: cell_multi_kernel<Real, OP_FULL2, BS><<<(unsigned)nb, BS, 0, s>>>(grids, ngrid, offsets, total, tabs, queue, qcount, rcache, uc, 0); break;
     case OP_HALF | OP_GENERAL: cell_multi_general_kernel<Real, OP_HALF><<<gen_blocks, gbs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
     case OP_FULL1 | OP_GENERAL: cell_multi_general_kernel<Real, OP_FULL1><<<gen_blocks, gbs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
     case OP_FULL2 | OP_GENERAL: cell_multi_general_kernel<Real, OP_FULL2><<<gen_blocks, gbs, 0, s>>>(grids, ngrid, offsets, tabs, queue, qcount); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+// nsmax: the largest source count of the grids in the call (1 selects the
+// single-source kernels, whose per-source state stays in registers).  cell_bs:
+// threads per block of the closed-form passes (256; anything else: 128).
+template <typename Real>
+cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
+                        const DevTable<Real> *tabs, int op, int nsmax, unsigned *queue, unsigned *qcount,
+                        Real *qrec, Real *rcache, int use_cache, int gen_blocks, int cell_bs, cudaStream_t s)
+{
+    if (total <= 0) return cudaSuccess;
+    if (op == OP_RATEDT_VERIFY && nsmax <= 1) return cudaSuccess;     // the single-source pass uses no hint
+    const int uc = use_cache && rcache ? 1 : 0;
+    if (nsmax <= 1)
+        return cell_bs == 256
+                   ? launch_cell_ns<Real, 1, 256>(grids, ngrid, offsets, total, tabs, op, queue, qcount, qrec, rcache, uc, gen_blocks, s)
+                   : launch_cell_ns<Real, 1, 128>(grids, ngrid, offsets, total, tabs, op, queue, qcount, qrec, rcache, uc, gen_blocks, s);
+    return cell_bs == 256
+               ? launch_cell_multi<Real, 256>(grids, ngrid, offsets, total, tabs, op, queue, qcount, rcache, uc, gen_blocks, s)
+               : launch_cell_multi<Real, 128>(grids, ngrid, offsets, total, tabs, op, queue, qcount, rcache, uc, gen_blocks, s);
 }
 
 template <typename Real> size_t queue_record_bytes() { return QREC * sizeof(Real); }
@@ -1001,10 +1007,10 @@ cudaError_t launch_finalize(const GridDev<Real> *grids, int ngrid, int stage, un
 
 template cudaError_t launch_cell<double>(const GridDev<double> *, int, const long long *, long long,
                                          const DevTable<double> *, int, int, unsigned *, unsigned *, double *, double *,
-                                         int, int, cudaStream_t);
+                                         int, int, int, cudaStream_t);
 template cudaError_t launch_cell<float>(const GridDev<float> *, int, const long long *, long long,
                                         const DevTable<float> *, int, int, unsigned *, unsigned *, float *, float *, int,
-                                        int, cudaStream_t);
+                                        int, int, cudaStream_t);
 template size_t queue_record_bytes<double>();
 template size_t queue_record_bytes<float>();
 template int cell_general_occupancy<double>(int);

@@ -90,10 +90,11 @@ enum { OP_RATEDT = 0, OP_HALF = 1, OP_FULL1 = 2, OP_FULL2 = 3, OP_RATEDT_VERIFY 
 // the same substep reads when use_cache is set: the transmitted fraction,
 // F(x0) and F'(x0) of single-source grids; F(x0), F'(x0) and the sum of the
 // sources' rate bounds when nsmax > 1 (the full step then recomputes).
+// cell_bs: threads per block of the closed-form passes, 128 or 256 (the general passes use 256).
 template <typename Real>
 cudaError_t launch_cell(const GridDev<Real> *grids, int ngrid, const long long *offsets, long long total,
                         const DevTable<Real> *tabs, int op, int nsmax, unsigned *queue, unsigned *qcount,
-                        Real *qrec, Real *rcache, int use_cache, int gen_blocks, cudaStream_t s);
+                        Real *qrec, Real *rcache, int use_cache, int gen_blocks, int cell_bs, cudaStream_t s);
 template <typename Real> size_t queue_record_bytes();
 template <typename Real> int cell_general_occupancy(int nsmax);
 // stage 0 also clears the queue lengths and the general passes' head counters

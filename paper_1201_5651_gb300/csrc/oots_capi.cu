@@ -112,6 +112,7 @@ struct oots_ctx {
     long long skip_publish = -1;
     int sweep_chunk = 0;               // planes per progress step of the sweep (0: default)
     int tile_align = 0;                // tile origins: 0 global multiples of the tile (x rows aligned), 1 the octant's
+    int cell_block = 0;                // threads per block of the closed-form passes: 128, 256, 0 = by source count
     size_t rsize = 8;
     void *d_x = nullptr, *d_n = nullptr, *d_xh = nullptr, *d_N1 = nullptr, *d_N2 = nullptr;
     void *d_stage = nullptr;           // ncell doubles: host arrays pass through it (allocated on first use)
@@ -169,6 +170,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     Real *d_nstar = nullptr;           // per grid 3 x MAX_SRC negligible-column thresholds (several sources)
     unsigned *d_qcount = nullptr;      // queue lengths of the half and full integrations
     int gen_blocks = 1;                // grid of the general pass
+    int cell_bs = 128;                 // threads per block of the closed-form passes
     int nblocks0 = 1, nblocks1 = 1;
     int nsmax = 1;                     // largest source count among the grids
     cudaGraph_t graph = nullptr;
@@ -451,6 +453,9 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         nblocks0 = sweep_occupancy<Real>(shape, 0) * nsm;
         nblocks1 = sweep_occupancy<Real>(shape, 1) * nsm;
         gen_blocks = cell_general_occupancy<Real>(nsmax) * nsm;
+        // closed-form passes: 128-thread blocks for many sources (a slow cell holds up fewer others),
+        // 256 for one source (cheap cells; fewer block set-ups), unless tuned
+        cell_bs = c0->cell_block > 0 ? c0->cell_block : (nsmax > 1 ? 128 : 256);
         return OOTS_OK;
     }
 
@@ -507,21 +512,21 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     {
         if (prof) prof->mark(0);
         CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op, nsmax, d_queue, d_qcount, d_qrec,
-                             d_rcache, use_cache ? 1 : 0, gen_blocks, s));
+                             d_rcache, use_cache ? 1 : 0, gen_blocks, cell_bs, s));
         if (prof) prof->mark(op == OP_RATEDT ? OOTS_K_RATEDT : (op == OP_HALF ? OOTS_K_HALF : OOTS_K_FULL));
         if (op == OP_RATEDT) {
             if (nsmax <= 1) return OOTS_OK;
             // several sources: the pass that checks the step hint
             if (prof) prof->mark(0);
             CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, OP_RATEDT_VERIFY, nsmax, d_queue,
-                                 d_qcount, d_qrec, d_rcache, use_cache ? 1 : 0, gen_blocks, s));
+                                 d_qcount, d_qrec, d_rcache, use_cache ? 1 : 0, gen_blocks, cell_bs, s));
             if (prof) prof->mark(OOTS_K_RATEDT_VERIFY);
             return OOTS_OK;
         }
         // the cells no closed form settles, one warp each
         if (prof) prof->mark(0);
         CU(launch_cell<Real>(d_grids, (int)ctxs.size(), d_offsets, total, d_tabs, op | OP_GENERAL, nsmax, d_queue,
-                             d_qcount, d_qrec, d_rcache, 0, gen_blocks, s));
+                             d_qcount, d_qrec, d_rcache, 0, gen_blocks, cell_bs, s));
         if (prof) prof->mark(op == OP_HALF ? OOTS_K_HALF_GENERAL : OOTS_K_FULL_GENERAL);
         return OOTS_OK;
     }
@@ -1320,6 +1325,9 @@ int oots_debug_set(oots_ctx *c, int key, long long value)
     } else if (key == 4) {
         if (value != 0 && value != 1) return fail(OOTS_E_INVAL, "tile alignment %lld", value);
         c->tile_align = (int)value;
+    } else if (key == 5) {
+        if (value != 0 && value != 128 && value != 256) return fail(OOTS_E_INVAL, "cell block %lld", value);
+        c->cell_block = (int)value;
     } else {
         return fail(OOTS_E_INVAL, "debug key %d", key);
     }

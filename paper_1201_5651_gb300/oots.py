@@ -262,6 +262,10 @@ class Context:
     def debug_set(self, key: int, value: int):
         return self._c(self.lib.oots_debug_set(self.h, int(key), int(value)))
 
+    def set_cell_block(self, threads: int):
+        """Threads per block of the closed-form per-cell passes: 128, 256 or 0 (default)."""
+        return self.debug_set(5, threads)
+
     def set_stream(self, stream_ptr):
         return self._c(self.lib.oots_set_stream(self.h, ctypes.c_void_p(stream_ptr) if stream_ptr else None))
 

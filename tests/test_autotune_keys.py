@@ -40,15 +40,19 @@ def test_cache_keys_separate_devices_and_precisions(tmp_path):
 
 
 class _FakeCtx:
-    """Stands in for a context: records the tile shape it is given; profiling is never reached."""
+    """Stands in for a context: records the tile shape and block size it is given; profiling is never reached."""
 
     def __init__(self, shape, precision):
         self.shape = shape
         self.precision = precision
         self.tile = None
+        self.cell_block = None
 
     def set_tile_shape(self, s):
         self.tile = s
+
+    def set_cell_block(self, b):
+        self.cell_block = b
 
     def profile_substep(self):
         raise AssertionError("a cached class must not be re-timed")
@@ -61,3 +65,21 @@ def test_tune_reuses_a_cached_class_without_timing(tmp_path):
     c = _FakeCtx((512, 512, 300), oots.OOTS_MIXED)       # (nz, ny, nx)
     assert autotune.tune(c, "GB300", 16, path=path) == 7
     assert c.tile == 7
+
+
+def test_a_cached_class_also_sets_the_per_cell_block_size(tmp_path):
+    """The block size of the closed-form passes is cached with the tile shape and
+    applied with it; an entry without one leaves the library's default."""
+    path = str(tmp_path / "tune.json")
+    k = autotune.plane_class(512, 512, 512, 16)
+    autotune._store(autotune.cache_key("GB300", oots.OOTS_MIXED, k), {"shape": 7, "cell_block": 128}, path)
+    c = _FakeCtx((512, 512, 512), oots.OOTS_MIXED)
+    assert autotune.tune(c, "GB300", 16, path=path) == 7
+    assert (c.tile, c.cell_block) == (7, 128)
+    assert autotune.lookup_cell_block("GB300", oots.OOTS_MIXED, k, path) == 128
+    k1 = autotune.plane_class(128, 128, 128, 1)
+    autotune._store(autotune.cache_key("GB300", oots.OOTS_MIXED, k1), {"shape": 2}, path)
+    c1 = _FakeCtx((128, 128, 128), oots.OOTS_MIXED)
+    assert autotune.tune(c1, "GB300", 1, path=path) == 2
+    assert c1.cell_block is None
+    assert autotune.lookup_cell_block("GB300", oots.OOTS_MIXED, k1, path) == 0

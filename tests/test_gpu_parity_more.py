@@ -128,3 +128,30 @@ def test_autotuned_shape_keeps_parity(tmp_path):
     assert abs(dt_g / dt - 1.0) <= 1e-10
     c.step(dt_g)
     assert float(np.max(np.abs(c.get_neutral_fraction() - x))) <= XTOL, shape
+
+
+@pytest.mark.parametrize("nsrc", [1, 3])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cell_block_sizes_agree(nsrc, precision):
+    """The closed-form passes give every cell the same result with 128- and
+    256-thread blocks (tuning key 5): the same steps, x bit for bit; the FP64
+    path also equals the oracle."""
+    w = inputs.small_random(n=26, ny=21, nz=19, seed=91 + nsrc, nsrc=nsrc, spectrum="bb")
+    out = {}
+    for bs in (128, 256):
+        c = oots.Context.from_workload(w, precision, scheme=3, K4=0.25)
+        c.set_cell_block(bs)
+        dts = []
+        for _ in range(3):
+            dts.append(c.compute_dt())
+            c.step(dts[-1])
+        out[bs] = (dts, c.get_neutral_fraction())
+    assert out[128][0] == out[256][0]
+    assert np.array_equal(out[128][1], out[256][1])
+    if precision == "fp64":
+        P = oracle.Problem.from_workload(w)
+        x = np.ascontiguousarray(w.x0.astype(np.float64))
+        t = 0.0
+        for _ in range(3):
+            t, *_ = P.substep(x, t, 1e300, scheme=3, K4=0.25)
+        assert float(np.max(np.abs(out[256][1] - x))) <= XTOL
