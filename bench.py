@@ -402,6 +402,10 @@ def bench_single(args, name, steps, warmup, rank, world, dev, flush, devname, wi
                 cf.set_tile_shape(0)
         cf.set_neutral_fraction(x_t0)
         cf.set_time(t0)
+        # the entry columns of the same state on both paths (float-float against double)
+        col_src = sorted({0, nsrc - 1})
+        cf.compute_dt()
+        col64 = {s_: cf.get_column_density(s_) for s_ in col_src}
         k64 = spec["k64"]
         ms64 = _timed_substeps(lambda: cf.run_substeps(1, t_end), cf.synchronize, sf, flush, k64, 1)
         ms64 = rank_max(ms64, world, f"cuda:{dev}")
@@ -411,6 +415,13 @@ def bench_single(args, name, steps, warmup, rank, world, dev, flush, devname, wi
         torch.cuda.empty_cache()
         cm.set_neutral_fraction(x_t0)
         cm.set_time(t0)
+        cm.compute_dt()
+        col_err = 0.0
+        for s_ in col_src:
+            nm = cm.get_column_density(s_)
+            col_err = max(col_err, float(np.max(np.abs(nm - col64[s_]) / np.maximum(col64[s_], 1e10))))
+            del nm
+        del col64
         cm.advance(tf)
         xm = cm.get_neutral_fraction()
         rm, rf = _reff(xm, w.dx, spec["n_oct"]), _reff(xf, w.dx, spec["n_oct"])
@@ -421,7 +432,9 @@ def bench_single(args, name, steps, warmup, rank, world, dev, flush, devname, wi
             "from_t_over_trec": t0 / trec, "t_over_trec": tf / trec, "fp64_substeps": k64 + 1,
             "reff_rel_err": abs(rm / rf - 1.0),
             "ionised_volume_rel_err": abs(float((1 - xm).sum()) / float((1 - xf).sum()) - 1.0),
-            "max_abs_dx": float(np.max(np.abs(xm - xf)))}
+            "max_abs_dx": float(np.max(np.abs(xm - xf))),
+            "column_rel_err": col_err,
+            "column_rel_err_sources": col_src}
     # end to end through the C ABI with host buffers: each step uploads the state
     # (oots_set_neutral_fraction), runs one substep and reads the state back
     # (oots_get_neutral_fraction), from and into pinned host memory

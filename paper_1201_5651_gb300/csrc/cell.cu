@@ -435,11 +435,38 @@ __device__ Real negligible_column(const GridDev<Real> &G, const DevTable<Real> *
     return T.Nnode[lo + 1];
 }
 
+// src_cell and src_lnamp from a source record (SrcSel): the same values, the same decisions
+template <typename Real>
+__device__ __forceinline__ float sel_lnamp(const SrcSel<Real> &S, int X, int Y, int Z, Real N, int &i, int &j, int &k)
+{
+    i = X >= S.v0 ? X - S.v0 : S.v0 - 1 - X;
+    j = Y >= S.v1 ? Y - S.v1 : S.v1 - 1 - Y;
+    k = Z >= S.v2 ? Z - S.v2 : S.v2 - 1 - Z;
+    float r2 = 1.0f;
+    if (!S.plane) {
+        const float c0 = i + 0.5f, c1 = j + 0.5f, c2 = k + 0.5f;
+        r2 = c0 * c0 + c1 * c1 + c2 * c2;
+    }
+    float lnp;
+    if (S.K < 0) {
+        lnp = S.msig * (float)N;
+    } else if (!(N > S.N0)) {
+        lnp = 0.0f;
+    } else if (N > S.Nhi) {
+        lnp = -__int_as_float(0x7f800000);
+    } else {
+        int kk = (int)floorf((__logf((float)N) - S.lnN_lo) * S.inv_dl) - 1;
+        kk = kk < 0 ? 0 : (kk > S.K - 1 ? S.K - 1 : kk);
+        lnp = (float)S.L[kk];
+    }
+    return S.lnamp0 + lnp - __logf(r2);
+}
+
 // Rate parameters of the sources whose bound exceeds e^lnthr, into
 // r[0 .. NK-1] (indices fixed at compile time, so r stays in registers).
-// Returns how many there are; NK + 1 when there are more than NK.
-// nstar (may be null): per source a column beyond which the source is left
-// out without forming its bound.
+// Returns how many there are; NK + 1 when there are more than NK.  sel: the
+// pass's source records; a source whose entry column is at or beyond its
+// record's negligible column is left out without forming its bound.
 // The entry columns of sources s0 .. s0+7 at cell g, loaded together (eight
 // loads in flight instead of one latency per source).
 template <typename Real>
@@ -450,9 +477,9 @@ __device__ __forceinline__ void load_columns8(const GridDev<Real> &G, const Real
 }
 
 template <typename Real, int NK>
-__device__ __forceinline__ int gather_rates(const GridDev<Real> &G, const Real *Ncol, const DevTable<Real> *tabs,
-                                            int X, int Y, int Z, long long g, Real n, float lnthr, SrcRate<Real> *r,
-                                            const Real *nstar)
+__device__ __forceinline__ int gather_rates_sel(const GridDev<Real> &G, const SrcSel<Real> *sel, const Real *Ncol,
+                                                const DevTable<Real> *tabs, int X, int Y, int Z, long long g, Real n,
+                                                float lnthr, SrcRate<Real> *r)
 {
     int cnt = 0;
     for (int s0 = 0; s0 < G.nsrc; s0 += 8) {
@@ -463,10 +490,10 @@ __device__ __forceinline__ int gather_rates(const GridDev<Real> &G, const Real *
             const int s = s0 + q;
             if (s >= G.nsrc) break;
             const Real N = Nb[q];
-            if (nstar && N >= nstar[s]) continue;
+            const SrcSel<Real> &S = sel[s];
+            if (N >= S.nst) continue;
             int i, j, k;
-            const float r2 = src_cell(G, s, X, Y, Z, i, j, k);
-            if (!(src_lnamp(G, tabs, s, r2, N) > lnthr)) continue;
+            if (!(sel_lnamp(S, X, Y, Z, N, i, j, k) > lnthr)) continue;
             if (cnt == NK) return NK + 1;
             SrcRate<Real> t;
             src_rate<Real>(t, G.qfac[s], G.tab[s], G.sigma0, G.dx, n, G.pcode[s] != 0, i, j, k, N, tabs);
@@ -530,7 +557,7 @@ __device__ __forceinline__ bool closed_form_from_F(Real c, Real x0, Real h, Real
 // |dx/dt| by far less than its rounding as long as the step comes out below
 // H; a second, verifying launch (verify = 1) recomputes every cell without
 // hint when it did not, and returns at once otherwise.  Per source, a column
-// beyond which it cannot reach the threshold anywhere (nstar, set by the
+// beyond which it cannot reach the threshold anywhere (SrcSel::nst, set by the
 // finalize kernel once per substep) skips even the bound.  RATEDT caches F,
 // F' and the sum of the bounds for the step that follows on the same columns
 // (A3's half step, A2's full step), which settles photon-free and slow cells
@@ -636,7 +663,8 @@ __global__ void __launch_bounds__(BS, (sizeof(Real) == 4 ? 1024 : 512) / BS) cel
                 // Eq. 4 with T fixed: K1 t_rec, K3 max(0.05, x)/|dx/dt|, K4/|dx/dt|,
                 // from the sources that can matter within the hint (their bounds);
                 // a cell that none of them reaches is photon-free (F = F' = 0).
-                const Real *nst = (G.nstar && !verify) ? G.nstar : nullptr;
+                // the records of this pass: with the hint's negligible columns, or none when verifying
+                const SrcSel<Real> *sel = G.sel + (verify ? 3 : 0) * MAX_SRC;
                 float ampsum = 0.0f;
                 Real F = Real(0), dF = Real(0);
                 for (int s0 = 0; s0 < G.nsrc; s0 += 8) {
@@ -647,10 +675,10 @@ __global__ void __launch_bounds__(BS, (sizeof(Real) == 4 ? 1024 : 512) / BS) cel
                         const int s = s0 + q;
                         if (s >= G.nsrc) break;
                         const Real N = Nb[q];
-                        if (nst && N >= nst[s]) continue;
+                        const SrcSel<Real> &S = sel[s];
+                        if (N >= S.nst) continue;
                         int i, j, k;
-                        const float r2 = src_cell(G, s, X, Y, Z, i, j, k);
-                        const float la = src_lnamp(G, tabs, s, r2, N);
+                        const float la = sel_lnamp(S, X, Y, Z, N, i, j, k);
                         if (!(la > lnthr)) continue;
                         ampsum += __expf(la);
                         SrcRate<Real> t;
@@ -712,8 +740,8 @@ __global__ void __launch_bounds__(BS, (sizeof(Real) == 4 ? 1024 : 512) / BS) cel
                 if (!done) {
                     SrcRate<Real> r[NACT];
                     const Real *Ncol = (OP == OP_FULL2) ? G.N2 : G.N1;
-                    const Real *nst = G.nstar ? G.nstar + (OP == OP_HALF ? 1 : 2) * MAX_SRC : nullptr;
-                    const int na = gather_rates<Real, NACT>(G, Ncol, tabs, X, Y, Z, g, n, lnthr, r, nst);
+                    const SrcSel<Real> *sel = G.sel + (OP == OP_HALF ? 1 : 2) * MAX_SRC;
+                    const int na = gather_rates_sel<Real, NACT>(G, sel, Ncol, tabs, X, Y, Z, g, n, lnthr, r);
                     if (na <= NACT) {
                         CellODE<Real> C;
                         C.ns = na; C.c = c; C.b0 = Real(0); C.r = r; C.tabs = tabs;
@@ -829,9 +857,9 @@ cell_multi_general_kernel(const GridDev<Real> *grids, int ngrid, const long long
         // in local memory; one instantiation of the integrator keeps the kernel's
         // code small (its lanes run apart through the root search and quadrature)
         SrcRate<Real> ra[MAX_SRC];
-        const Real *nst = G.nstar ? G.nstar + (OP == OP_HALF ? 1 : 2) * MAX_SRC : nullptr;
+        const SrcSel<Real> *sel = G.sel + (OP == OP_HALF ? 1 : 2) * MAX_SRC;
         CellODE<Real> C;
-        C.ns = gather_rates<Real, MAX_SRC>(G, Ncol, tabs, X, Y, Z, g, n, lnthr, ra, nst);
+        C.ns = gather_rates_sel<Real, MAX_SRC>(G, sel, Ncol, tabs, X, Y, Z, g, n, lnthr, ra);
         C.c = G.alpha * n; C.b0 = Real(0); C.r = ra; C.tabs = tabs;
         if (!integrate_prelude<Real, MAX_SRC>(C, x0, h, G.sigma0, R, F0, dF0, f0))
             R = integrate_general<Real, MAX_SRC>(C, x0, h, G.sigma0, R, F0, dF0, f0, GroupEval<W>{lane, gbase, gmask});
@@ -898,12 +926,12 @@ __global__ void finalize_kernel(const GridDev<Real> *grids, int ngrid, int stage
         }
         st->dt_bits = 0xffffffffffffffffull;
         const GridDev<Real> &G = grids[gi];
-        if (G.nstar && dt > 0.0) {
-            // thresholds of the next dt pass (its hint, 4 dt_last), the half step and the full step
+        if (G.sel && dt > 0.0) {
+            // negligible columns of the next dt pass (its hint, 4 dt_last), the half step and the full step
             for (int s = 0; s < G.nsrc; s++) {
-                G.nstar[s] = negligible_column<Real>(G, tabs, s, st->lnthr[0]);
-                G.nstar[MAX_SRC + s] = negligible_column<Real>(G, tabs, s, st->lnthr[1]);
-                G.nstar[2 * MAX_SRC + s] = negligible_column<Real>(G, tabs, s, st->lnthr[2]);
+                G.sel[s].nst = negligible_column<Real>(G, tabs, s, st->lnthr[0]);
+                G.sel[MAX_SRC + s].nst = negligible_column<Real>(G, tabs, s, st->lnthr[1]);
+                G.sel[2 * MAX_SRC + s].nst = negligible_column<Real>(G, tabs, s, st->lnthr[2]);
             }
         }
         st->bud_step[0] = st->sumQ * dt;

@@ -167,7 +167,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
     unsigned *d_queue = nullptr;       // cells left to the general pass (one entry per cell at most)
     Real *d_qrec = nullptr;            // their closed-form results (single-source launch sets)
     Real *d_rcache = nullptr;          // per cell: transmitted fraction, F(x0), F'(x0) from the dt pass
-    Real *d_nstar = nullptr;           // per grid 3 x MAX_SRC negligible-column thresholds (several sources)
+    SrcSel<Real> *d_sel = nullptr;     // per grid 4 x MAX_SRC source records of the selection (several sources)
     unsigned *d_qcount = nullptr;      // queue lengths of the half and full integrations
     int gen_blocks = 1;                // grid of the general pass
     int cell_bs = 128;                 // threads per block of the closed-form passes
@@ -199,7 +199,7 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
         cudaFree(d_queue);
         cudaFree(d_qrec);
         cudaFree(d_rcache);
-        cudaFree(d_nstar);
+        cudaFree(d_sel);
         cudaFree(d_qcount);
     }
 
@@ -391,12 +391,37 @@ template <typename Real> struct LaunchSet : LaunchSetBase {
             for (auto &G : grids) G.nbx = G.nby = G.nbz = 0;
         }
         if (nsmax > 1) {
-            // no threshold until the first step sets them (+inf: every source is looked at)
-            const size_t nn = grids.size() * 3 * MAX_SRC;
-            std::vector<Real> inf(nn, std::numeric_limits<Real>::infinity());
-            CU(cudaMalloc(&d_nstar, nn * sizeof(Real)));
-            CU(cudaMemcpy(d_nstar, inf.data(), nn * sizeof(Real), cudaMemcpyHostToDevice));
-            for (size_t g = 0; g < grids.size(); g++) grids[g].nstar = d_nstar + g * 3 * MAX_SRC;
+            // each source's selection record, four copies per grid (dt pass, half step, full
+            // step, verifying dt pass); no negligible column until the first step sets them
+            const size_t nn = grids.size() * 4 * MAX_SRC;
+            std::vector<SrcSel<Real>> sel(nn);
+            memset(sel.data(), 0, nn * sizeof(SrcSel<Real>));
+            for (size_t g = 0; g < grids.size(); g++) {
+                const GridDev<Real> &G = grids[g];
+                for (int s = 0; s < G.nsrc; s++) {
+                    SrcSel<Real> S;
+                    memset(&S, 0, sizeof(S));
+                    S.nst = std::numeric_limits<Real>::infinity();
+                    S.lnamp0 = G.lnamp0[s];
+                    S.v0 = G.vtx[s][0]; S.v1 = G.vtx[s][1]; S.v2 = G.vtx[s][2];
+                    S.plane = G.pcode[s] != 0;
+                    S.msig = -(float)G.sigma0;
+                    S.K = -1;
+                    if (G.tab[s] >= 0) {
+                        const DevTable<Real> &T = tabs[G.tab[s]];
+                        S.K = T.K;
+                        S.N0 = T.N0;
+                        S.Nhi = T.Nhi;
+                        S.L = T.L;
+                        S.lnN_lo = (float)T.lnN_lo;
+                        S.inv_dl = (float)T.inv_dl;
+                    }
+                    for (int k = 0; k < 4; k++) sel[(g * 4 + k) * MAX_SRC + s] = S;
+                }
+            }
+            CU(cudaMalloc(&d_sel, nn * sizeof(SrcSel<Real>)));
+            CU(cudaMemcpy(d_sel, sel.data(), nn * sizeof(SrcSel<Real>), cudaMemcpyHostToDevice));
+            for (size_t g = 0; g < grids.size(); g++) grids[g].sel = d_sel + g * 4 * MAX_SRC;
         }
         CU(cudaMalloc(&d_grids, grids.size() * sizeof(GridDev<Real>)));
         CU(cudaMemcpy(d_grids, grids.data(), grids.size() * sizeof(GridDev<Real>), cudaMemcpyHostToDevice));

@@ -61,6 +61,21 @@ struct DevState {
                               // (H = dt/2) and the full step's (H = dt); [3] unused
 };
 
+// What the many-source passes read of one source to decide whether it can
+// matter at a cell (Mackey 2012 Sect. 2 rate, bounded): one record of a few
+// 16-byte words instead of a dozen scattered descriptor reads.
+template <typename Real> struct __align__(16) SrcSel {
+    Real nst;                // negligible column of the pass (+inf: none)
+    Real N0, Nhi;            // tabulated: first and last node column
+    const Real *L;           // tabulated: node values ln(P/Q)
+    float lnamp0;            // ln(qfac sigma0 dx)
+    float lnN_lo, inv_dl;    // tabulated: table axis (as float)
+    float msig;              // monochromatic: -sigma0 (as float)
+    int v0, v1, v2;          // vertex
+    int K;                   // tabulated: nodes; -1: monochromatic
+    int plane;               // plane-parallel source
+};
+
 // Description of one grid for the kernels (Real = float or double).
 template <typename Real> struct GridDev {
     int nx, ny, nz;
@@ -85,8 +100,9 @@ template <typename Real> struct GridDev {
                               // brick (bx, by, bz) of nbx x nby x nbz holds cells bx*TX.., by*8.., bz*8..,
                               // x fastest, TX = the tile's x extent
     int nbx, nby, nbz;
-    Real *nstar;              // 3 x MAX_SRC entry columns beyond which a source cannot matter for the
-                              // dt pass (step hint), the half step and the full step (nullptr: none)
+    SrcSel<Real> *sel;        // 4 x MAX_SRC source records for the dt pass (nst: the column beyond which
+                              // a source cannot matter within the step hint), the half step, the full
+                              // step and the verifying dt pass (nst = +inf); nullptr: one source
     DevState *st;
 };
 
