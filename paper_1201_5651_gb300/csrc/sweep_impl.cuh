@@ -574,13 +574,14 @@ sweep_kernel(SweepParams<Real> P)
                             } else if (MODE == 0 && (mode & 0x20)) {
                                 // tied dominant axes: the average over the tied axes of
                                 // each axis's normalised interpolation, as weighted
-                                // differences to the a0-1 neighbour of the first tied axis
-                                // (the weights of all terms sum to one)
+                                // differences to the neighbour one step back along every
+                                // tied axis (it always carries weight; the weights of all
+                                // terms sum to one)
                                 const int idx[3] = {i, j, k};
                                 const int c2[3] = {2 * i + 1, 2 * j + 1, 2 * k + 1};
                                 const int cm = max(c2[0], max(c2[1], c2[2]));
-                                const int a0 = c2[0] == cm ? 0 : 1;
-                                const Col Nref = sN[h - str_a(a0)];
+                                const Col Nref = sN[h - (c2[0] == cm ? str_a(0) : 0) - (c2[1] == cm ? str_a(1) : 0) -
+                                                    (c2[2] == cm ? str_a(2) : 0)];
                                 const Real inv_nt = Real(1) / Real((c2[0] == cm) + (c2[1] == cm) + (c2[2] == cm));
                                 Real d = Real(0);
 #pragma unroll

@@ -89,7 +89,11 @@ template <typename Real, int TX> constexpr size_t sweep_tp_smem()
 // the upwind layer (c_t/c_a for the t-1 neighbour) times W, normalised; the
 // tied axes' interpolations are averaged.  Neighbours outside the octant are
 // dropped.  Written as weighted differences to one reference neighbour, so
-// the float-float column is not rounded to float before the increment.
+// the float-float column is not rounded to float before the increment.  The
+// reference is the neighbour one step back along every tied axis, which
+// always carries weight (with three tied axes all of it): a neighbour that
+// carries none would make the result a difference of columns far larger
+// than itself near the source vertex.
 template <typename Real, int TX>
 __device__ __forceinline__ typename ColT<Real>::type
 sc_entry_general(const typename ColT<Real>::type *sN, const Real *sW, int h, const int idx[3])
@@ -99,7 +103,7 @@ sc_entry_general(const typename ColT<Real>::type *sN, const Real *sW, int h, con
     const int c2[3] = {2 * idx[0] + 1, 2 * idx[1] + 1, 2 * idx[2] + 1};
     const int cm = max(c2[0], max(c2[1], c2[2]));
     if (cm == 1) return ColT<Real>::zero();                 // the cell at the vertex
-    const int sref = c2[0] == cm ? str[0] : (c2[1] == cm ? str[1] : str[2]);   // first tied axis
+    const int sref = (c2[0] == cm ? str[0] : 0) + (c2[1] == cm ? str[1] : 0) + (c2[2] == cm ? str[2] : 0);
     const typename ColT<Real>::type Nref = sN[h - sref];
     const Real inv_nt = Real(1) / Real((c2[0] == cm) + (c2[1] == cm) + (c2[2] == cm));
     Real d = Real(0);
