@@ -247,9 +247,10 @@ def kernel_bytes_per_cell(kind, rsz, nsrc, n_array):
 
 
 def step_bytes_per_cell(nsrc, n_array):
-    """Algorithmic HBM bytes of a whole A3 mixed substep per cell:
-    28 B for one source and a density array, 20 B with uniform density,
-    28 S + 32 B for S sources."""
+    """Algorithmic HBM bytes per cell of a whole A3 mixed substep in its fused form
+    (the dt criterion folded into the first trace, both integrations into the
+    second): 28 B for one source and a density array, 20 B with uniform
+    density, 28 S + 32 B for S sources."""
     if nsrc <= 1:
         return 28 if n_array else 20
     return 28 * nsrc + 32
