@@ -222,7 +222,6 @@ __device__ __forceinline__ void tp_load4(const double *p, double v[4])
 
 // compile-time constants passed to the kernel's generic lambdas
 template <int V> struct TpInt { static constexpr int value = V; };
-template <bool V> struct TpBool { static constexpr bool value = V; };
 
 template <typename Real, int TX>
 __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? (TX == 8 ? 16 : 9) : 8) sweep_tp_kernel(SweepParams<Real> P)
@@ -301,40 +300,35 @@ __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? (TX == 8 ? 16 : 9) : 8
         const int k_lo = max(-o0[2], 0), k_hi = min(J.ext[2] - o0[2], 8);
         if (G.nxb != nullptr) {
             // the tile's brick (its index set with the work list); thread tid
-            // takes brick cells 4 (tid + 64 v) .. +3.  A tile wholly inside its
-            // octant skips the range tests (compile-time flag).
+            // takes brick cells 4 (tid + 64 v) .. +3
             const Real *brick = reinterpret_cast<const Real *>(P.bricks) + (long long)it.brick * L::NC;
-            auto prepass = [&](auto FULL_) {
-                constexpr bool full = decltype(FULL_)::value;
 #pragma unroll
-                for (int v = 0; v < L::NC / 256; v++) {
-                    const int e0 = 4 * (tid + 64 * v);
-                    const int bj = (e0 / TX) % 8, bk = e0 / (TX * 8);
-                    const int lj = J.sg[1] > 0 ? bj : 7 - bj, lk = J.sg[2] > 0 ? bk : 7 - bk;
-                    const bool row_in = full || (lj >= j_lo && lj < j_hi && lk >= k_lo && lk < k_hi);
-                    Real nxv[4];
-                    if (row_in) tp_load4(brick + e0, nxv);
-                    const Real c1 = Real(o0[1] + lj) + Real(0.5), c2 = Real(o0[2] + lk) + Real(0.5);
+            for (int v = 0; v < L::NC / 256; v++) {
+                const int e0 = 4 * (tid + 64 * v);
+                const int bj = (e0 / TX) % 8, bk = e0 / (TX * 8);
+                const int lj = J.sg[1] > 0 ? bj : 7 - bj, lk = J.sg[2] > 0 ? bk : 7 - bk;
+                const bool row_in = lj >= j_lo && lj < j_hi && lk >= k_lo && lk < k_hi;
+                Real nxv[4];
+                if (row_in) tp_load4(brick + e0, nxv);
+                const Real c1 = Real(o0[1] + lj) + Real(0.5), c2 = Real(o0[2] + lk) + Real(0.5);
 #pragma unroll
-                    for (int c = 0; c < 4; c++) {
-                        const int bi = e0 % TX + c;
-                        const int li = J.sg[0] > 0 ? bi : TX - 1 - bi;
-                        const int h = L::h(li, lj, lk);
-                        Real dN = Real(0), wf = Real(0);
-                        if (full || (row_in && li >= i_lo && li < i_hi)) {
-                            const Real c0 = Real(o0[0] + li) + Real(0.5);
-                            const Real ds =
-                                dx * tp_sqrt(c0 * c0 + c1 * c1 + c2 * c2) * tp_rcp(m_max(c0, m_max(c1, c2)));
-                            dN = nxv[c] * ds;
-                            wf = tp_rcp(m_max(sig * dN, tau0));
-                        }
-                        sN[h] = ColT<Real>::zero();
-                        sW[h] = wf;
-                        sDI[h] = dN;
+                for (int c = 0; c < 4; c++) {
+                    const int bi = e0 % TX + c;
+                    const int li = J.sg[0] > 0 ? bi : TX - 1 - bi;
+                    const int h = L::h(li, lj, lk);
+                    Real dN = Real(0), wf = Real(0);
+                    if (row_in && li >= i_lo && li < i_hi) {
+                        const Real c0 = Real(o0[0] + li) + Real(0.5);
+                        const Real ds =
+                            dx * tp_sqrt(c0 * c0 + c1 * c1 + c2 * c2) * tp_rcp(m_max(c0, m_max(c1, c2)));
+                        dN = nxv[c] * ds;
+                        wf = tp_rcp(m_max(sig * dN, tau0));
                     }
+                    sN[h] = ColT<Real>::zero();
+                    sW[h] = wf;
+                    sDI[h] = dN;
                 }
-            };
-            prepass(TpBool<false>{});
+            }
         } else {
 #pragma unroll
             for (int b = 0; b < TX; b += 4) {
@@ -408,24 +402,22 @@ __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? (TX == 8 ? 16 : 9) : 8
         else if (lo1 > hi0 && lo1 > hi2) pure = 1;
         else if (lo2 > hi0 && lo2 > hi1) pure = 2;
 
-        // Layer by layer along the dominant axis a, with the axis and whether the
-        // tile lies wholly inside the octant fixed at compile time (the halo
-        // strides become immediate offsets, the range tests drop out).
+        // Layer by layer along the dominant axis a, the axis fixed at compile
+        // time (the halo strides become immediate offsets).
         // a = 0: this thread's cell (l, c8, r8), transverse t1 = y, t2 = z;
         // a = 1 (t1 = z, t2 = x) and a = 2 (t1 = x, t2 = y): cells (li, lb) with
         // lb the other transverse index, li = tid % TX, lb = tid / TX + q 64/TX.
-        auto layers = [&](auto A_, auto FULL_) {
+        auto layers = [&](auto A_) {
             constexpr int a = decltype(A_)::value;
-            constexpr bool full = decltype(FULL_)::value;
             constexpr int sa = a == 0 ? 1 : (a == 1 ? SY : SZ);
             constexpr int s1 = a == 0 ? SY : (a == 1 ? SZ : 1);
             constexpr int s2 = a == 0 ? SZ : (a == 1 ? 1 : SY);
             if constexpr (a == 0) {
                 const int lj = c8, lk = r8;
-                const bool col_in = full || (lj >= j_lo && lj < j_hi && lk >= k_lo && lk < k_hi);
+                const bool col_in = lj >= j_lo && lj < j_hi && lk >= k_lo && lk < k_hi;
                 const Real c1 = Real(2 * (o0[1] + lj) + 1), c2 = Real(2 * (o0[2] + lk) + 1);
                 for (int l = 0; l < TX; l++) {
-                    if (col_in && (full || (l >= i_lo && l < i_hi))) {
+                    if (col_in && l >= i_lo && l < i_hi) {
                         const int h = L::h(l, lj, lk);
                         const Real ica = tp_rcp(Real(2 * (o0[0] + l) + 1));
                         const Col Nin = sc_entry_axis<Real>(sN, sW, h - sa, s1, s2, c1 * ica, c2 * ica);
@@ -440,15 +432,15 @@ __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? (TX == 8 ? 16 : 9) : 8
                 const int la_lo = a == 1 ? j_lo : k_lo, la_hi = a == 1 ? j_hi : k_hi;
                 const int lb_lo = a == 1 ? k_lo : j_lo, lb_hi = a == 1 ? k_hi : j_hi;
                 const int li = tid % TX;
-                const bool i_in = full || (li >= i_lo && li < i_hi);
+                const bool i_in = li >= i_lo && li < i_hi;
                 const Real cx = Real(2 * (o0[0] + li) + 1);
                 for (int l = 0; l < 8; l++) {
-                    if ((full || (l >= la_lo && l < la_hi)) && i_in) {
+                    if (l >= la_lo && l < la_hi && i_in) {
                         const Real ica = tp_rcp(Real(2 * (oa + l) + 1));
 #pragma unroll
                         for (int q = 0; q < NQ; q++) {
                             const int lb = tid / TX + q * (64 / TX);
-                            if (full || (lb >= lb_lo && lb < lb_hi)) {
+                            if (lb >= lb_lo && lb < lb_hi) {
                                 const int h = a == 1 ? L::h(li, l, lb) : L::h(li, lb, l);
                                 const Real cb = Real(2 * (ob + lb) + 1);
                                 // a = 1: g1 for the z-1 neighbour, g2 for x-1; a = 2: g1 for x-1, g2 for y-1
@@ -464,9 +456,9 @@ __global__ void __launch_bounds__(64, sizeof(Real) == 4 ? (TX == 8 ? 16 : 9) : 8
             }
         };
         if (pure >= 0) {
-            if (pure == 0) layers(TpInt<0>{}, TpBool<false>{});
-            else if (pure == 1) layers(TpInt<1>{}, TpBool<false>{});
-            else layers(TpInt<2>{}, TpBool<false>{});
+            if (pure == 0) layers(TpInt<0>{});
+            else if (pure == 1) layers(TpInt<1>{});
+            else layers(TpInt<2>{});
         } else {
             // plane by plane (li + lj + lk = m), one thread per (lj, lk) column;
             // cells with one dominant axis take the cheap form, tied cells the
