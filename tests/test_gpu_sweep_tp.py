@@ -158,3 +158,33 @@ def test_mixed_columns_near_source_vertices():
         rel = np.abs(nm - nf) / np.maximum(nf, 1e10)
         assert float(rel.max()) <= 2e-3, (s, float(rel.max()))
         assert float(np.percentile(rel, 99.9)) <= 1e-6, s
+
+
+@pytest.mark.parametrize("shape", [TP, TP16])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_on_throughput_tiles_matches_solo_runs(shape, precision):
+    """Grids of different sizes and source counts in one batch on the throughput
+    tiles (one packing launch for all grids, tile items carrying their grid, the
+    per-tile end-time check of launches with several grids): each grid ends where
+    its own run ends, bit for bit, although the grids reach their end times at
+    different substeps."""
+    ws = [inputs.small_random(n=n, ny=n - 2, nz=n - 3, seed=70 + n, nsrc=k, spectrum="bb")
+          for n, k in ((14, 1), (20, 3), (17, 2))]
+    ends = [f * w.t_rec for f, w in zip((0.01, 0.03, 0.02), ws)]
+    solo = []
+    for w, te in zip(ws, ends):
+        c = oots.Context.from_workload(w, precision, scheme=3, K4=0.25)
+        c.set_tile_shape(shape)
+        _, nsub = c.advance(te)
+        solo.append((nsub, c.get_neutral_fraction()))
+    ctxs = []
+    for w in ws:
+        c = oots.Context.from_workload(w, precision, scheme=3, K4=0.25)
+        c.set_tile_shape(shape)
+        ctxs.append(c)
+    b = oots.Batch(ctxs)
+    nsub = b.advance(ends)
+    b.close()
+    for g, (c, (ns, xs)) in enumerate(zip(ctxs, solo)):
+        assert nsub[g] == ns, (g, nsub[g], ns)
+        assert np.array_equal(c.get_neutral_fraction(), xs), g
