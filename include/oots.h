@@ -280,11 +280,14 @@ int oots_array_device(oots_ctx *ctx, int kind, int source, void **ptr, unsigned 
 
 /* ---- batches ------------------------------------------------------------------------------- */
 
-/* Group n contexts of the same device and precision, each with its grid,
- * sources, scheme (A2 or A3) and criteria, so that every substep of all of
- * them runs as one persistent sweep launch and one launch per per-cell pass.
- * The contexts stay owned by the caller and must outlive the batch; they
- * must not be stepped individually while batched. */
+/* Group n contexts (1 <= n <= 65535) of the same device and precision, each
+ * with its grid, sources, scheme (A2 or A3) and criteria, so that every
+ * substep of all of them runs as one persistent sweep launch and one launch
+ * per per-cell pass.  The contexts stay owned by the caller and must outlive
+ * the batch; they must not be stepped individually while batched.  Errors:
+ * E_INVAL (arguments, n out of range, contexts that differ in device,
+ * precision or fixed/adaptive dt), E_UNSUPPORTED (A1 or mixed schemes),
+ * E_STATE (a context already batched). */
 int oots_batch_create(oots_batch **out, oots_ctx *const *ctxs, int n);
 
 /* Advance every context of the batch to its own end time t_end_each[i];

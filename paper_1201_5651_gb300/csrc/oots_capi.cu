@@ -1457,6 +1457,7 @@ int oots_batch_create(oots_batch **out, oots_ctx *const *ctxs, int n)
 {
     if (!out || !ctxs || n <= 0) return fail(OOTS_E_INVAL, "batch arguments");
     *out = nullptr;
+    if (n > 65535) return fail(OOTS_E_INVAL, "%d contexts in one batch (at most 65535)", n);
     for (int i = 0; i < n; i++) {
         if (!ctxs[i]) return fail(OOTS_E_INVAL, "context %d is NULL", i);
         if (ctxs[i]->device != ctxs[0]->device || ctxs[i]->precision != ctxs[0]->precision)
