@@ -380,42 +380,10 @@ cell_general_kernel(const GridDev<Real> *grids, int ngrid, const long long *offs
 // rates of the sources kept are then formed exactly, in a few registers.
 constexpr int NACT = 4;        // sources the closed-form passes hold in registers
 
-// ln P(N)/Q rounded up: the node value one interval below N's
-template <typename Real>
-__device__ __forceinline__ float lnp_upper(const DevTable<Real> &T, Real N)
-{
-    if (!(N > T.N0)) return 0.0f;
-    if (N > T.Nhi) return -__int_as_float(0x7f800000);
-    int k = (int)floorf((__logf((float)N) - (float)T.lnN_lo) * (float)T.inv_dl) - 1;
-    k = k < 0 ? 0 : (k > T.K - 1 ? T.K - 1 : k);
-    return (float)T.L[k];
-}
-
-// Octant-local indices of cell (X,Y,Z) for source s and r2 = |c|^2 in units
-// of dx^2 (1 for a plane source, whose rate shares photons per unit area).
-template <typename Real>
-__device__ __forceinline__ float src_cell(const GridDev<Real> &G, int s, int X, int Y, int Z, int &i, int &j, int &k)
-{
-    i = X >= G.vtx[s][0] ? X - G.vtx[s][0] : G.vtx[s][0] - 1 - X;
-    j = Y >= G.vtx[s][1] ? Y - G.vtx[s][1] : G.vtx[s][1] - 1 - Y;
-    k = Z >= G.vtx[s][2] ? Z - G.vtx[s][2] : G.vtx[s][2] - 1 - Z;
-    if (G.pcode[s]) return 1.0f;
-    const float c0 = i + 0.5f, c1 = j + 0.5f, c2 = k + 0.5f;
-    return c0 * c0 + c1 * c1 + c2 * c2;
-}
-
-// ln of the bound amp of source s (entry column N) at a cell with r2
-template <typename Real>
-__device__ __forceinline__ float src_lnamp(const GridDev<Real> &G, const DevTable<Real> *tabs, int s, float r2, Real N)
-{
-    const float lnp = G.tab[s] < 0 ? -(float)G.sigma0 * (float)N : lnp_upper(tabs[G.tab[s]], N);
-    return G.lnamp0[s] + lnp - __logf(r2);
-}
-
 // The entry column beyond which source s cannot reach the threshold e^lnthr at
 // any cell: r2 >= 3/4, so amp <= e^lnthr whenever ln P/Q <= lnthr - ln(qfac
 // sigma0 dx) + ln(3/4).  Monochromatic: ln P/Q = -sigma0 N.  Tabulated: the
-// bound lnp_upper reads the node one interval below N, so N at or above the
+// bound (sel_lnamp) reads the node one interval below N, so N at or above the
 // node after the first node below the target qualifies.  +inf: never.
 template <typename Real>
 __device__ Real negligible_column(const GridDev<Real> &G, const DevTable<Real> *tabs, int s, float lnthr)
@@ -435,7 +403,12 @@ __device__ Real negligible_column(const GridDev<Real> &G, const DevTable<Real> *
     return T.Nnode[lo + 1];
 }
 
-// src_cell and src_lnamp from a source record (SrcSel): the same values, the same decisions
+// ln of the bound amp of one source at cell (X, Y, Z) with entry column N,
+// from the source's record, and the cell's octant-local indices (i, j, k).
+// r2 = |c|^2 in units of dx^2 (1 for a plane source, whose rate shares
+// photons per unit area); ln P/Q rounded up: -sigma0 N (monochromatic) or the
+// table node one interval below N's (tabulated; 0 below the table, -inf
+// above it).
 template <typename Real>
 __device__ __forceinline__ float sel_lnamp(const SrcSel<Real> &S, int X, int Y, int Z, Real N, int &i, int &j, int &k)
 {
@@ -462,11 +435,6 @@ __device__ __forceinline__ float sel_lnamp(const SrcSel<Real> &S, int X, int Y, 
     return S.lnamp0 + lnp - __logf(r2);
 }
 
-// Rate parameters of the sources whose bound exceeds e^lnthr, into
-// r[0 .. NK-1] (indices fixed at compile time, so r stays in registers).
-// Returns how many there are; NK + 1 when there are more than NK.  sel: the
-// pass's source records; a source whose entry column is at or beyond its
-// record's negligible column is left out without forming its bound.
 // The entry columns of sources s0 .. s0+7 at cell g, loaded together (eight
 // loads in flight instead of one latency per source).
 template <typename Real>
@@ -476,6 +444,11 @@ __device__ __forceinline__ void load_columns8(const GridDev<Real> &G, const Real
     for (int q = 0; q < 8; q++) Nb[q] = s0 + q < G.nsrc ? Ncol[(long long)(s0 + q) * G.ncell + g] : Real(0);
 }
 
+// Rate parameters of the sources whose bound exceeds e^lnthr, into
+// r[0 .. NK-1] (indices fixed at compile time, so r stays in registers).
+// Returns how many there are; NK + 1 when there are more than NK.  sel: the
+// pass's source records; a source whose entry column is at or beyond its
+// record's negligible column is left out without forming its bound.
 template <typename Real, int NK>
 __device__ __forceinline__ int gather_rates_sel(const GridDev<Real> &G, const SrcSel<Real> *sel, const Real *Ncol,
                                                 const DevTable<Real> *tabs, int X, int Y, int Z, long long g, Real n,
